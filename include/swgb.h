@@ -1,0 +1,161 @@
+/*
+ * swgb -- score-only Smith-Waterman protein database search on one GB300.
+ *
+ * The operation (Sec. 2.2, Eqs. 1-3 of "SYCL vs CUDA performance portability
+ * with SW#", arXiv 2412.08308): for every query Q (length m) and every
+ * database sequence D (length n) compute the local alignment score
+ *
+ *   S(Q, D) = max over i, j of H[i][j], with
+ *   H[i][j] = max(0, H[i-1][j-1] + SM(Q[i], D[j]), E[i][j], F[i][j])   (Eq. 1)
+ *   E[i][j] = max(H[i][j-1] - Go, E[i][j-1] - Ge)                      (Eq. 2)
+ *   F[i][j] = max(H[i-1][j] - Go, F[i-1][j] - Ge)                      (Eq. 3)
+ *
+ * with H, E, F = 0 on row 0 and column 0.  The paper's database search scores
+ * proteins with BLOSUM62 and gap penalties 10/2 (Sec. 4.1).
+ *
+ * Conventions of this interface
+ * -----------------------------
+ *  - Residues are uint8 codes 0..19 (the caller's alphabet order).  Any other
+ *    code is rejected with SW_EINVAL.  Zero-length sequences are legal and
+ *    score 0.
+ *  - submat is a row-major 20x20 int8 table: row = query residue, column =
+ *    database residue.  Entries must lie in [-64, 63].
+ *  - Gaps: a run of k gap positions costs gap_open + k * gap_extend.  In Eqs.
+ *    2-3 that is Go = gap_open + gap_extend, Ge = gap_extend; "10/2" gives
+ *    10 + 2k.  Both penalties must be >= 0 and gap_open + 2*gap_extend <= 1024.
+ *  - Sequence sets are passed as one concatenated residue array plus an int64
+ *    offset array with n+1 entries (offsets[0] = 0, non-decreasing,
+ *    offsets[n] = total residues).
+ *  - Scores are int32, laid out [n_queries][n_db] in the caller's order.
+ *  - Every entry point returns an SW_* status; on failure sw_last_error()
+ *    gives a message (thread-local, valid until the next call on the thread).
+ *    Nothing is thrown across this interface.
+ *  - One CUDA device: the current device of the calling thread when the
+ *    database is prepared.  All work is ordered on the caller's stream
+ *    (a cudaStream_t passed as void*; NULL = legacy default stream).
+ *
+ * Ownership: the caller owns every buffer it passes.  sw_db and sw_queries
+ * own the device memory they allocate and release it in their *_free call.
+ * Handles are not thread-safe: use one handle per thread or serialise.
+ */
+#ifndef SWGB_H
+#define SWGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define SW_OK 0
+#define SW_EINVAL 1   /* invalid argument: bad code, offsets, penalties, sizes, pointers */
+#define SW_ENOMEM 2   /* device or host allocation failed */
+#define SW_ECUDA 3    /* a CUDA runtime call failed */
+#define SW_ETIMEOUT 4 /* a bounded device-side wait expired; results are invalid */
+
+/* arithmetic forms of the dynamic-programming kernels */
+#define SW_MODE_INT32 0  /* plain 32-bit cells: the paper's Algorithm 1 body, one cell per lane op */
+#define SW_MODE_PACKED 1 /* two 16-bit cells per 32-bit word, saturation flags, exact int32 rescue */
+
+typedef struct sw_db sw_db;
+typedef struct sw_queries sw_queries;
+
+/*
+ * sw_db_prepare -- pack a protein database into device memory (one-time).
+ *
+ * Sorts the sequences by length, pads each to a multiple of 16 residues with
+ * a neutral pad code, and uploads the packed residues, the permutation back
+ * to caller order and per-sequence metadata to the current device.  The
+ * packed database stays resident until sw_db_free.  (Sec. 3.1: SW# assigns
+ * database sequences to its kernels by length.)
+ *
+ *   residues  host pointer, offsets[n_seqs] bytes of codes 0..19
+ *   offsets   host pointer, n_seqs + 1 int64 entries
+ *   n_seqs    >= 0 (an empty database is legal)
+ *   stream    cudaStream_t for the upload; the call returns after it completes
+ *   out       receives the new handle
+ *
+ * Errors: SW_EINVAL (null pointers, bad offsets or codes), SW_ENOMEM, SW_ECUDA.
+ */
+int sw_db_prepare(const uint8_t *residues, const int64_t *offsets, int64_t n_seqs,
+                  void *stream, sw_db **out);
+
+/* Release a database and its device memory.  NULL is accepted. */
+int sw_db_free(sw_db *db);
+
+/* Sizes of a prepared database: sequence count, residue count, device bytes. */
+int sw_db_stats(const sw_db *db, int64_t *n_seqs, int64_t *residues, int64_t *device_bytes);
+
+/*
+ * sw_queries_prepare -- upload a batch of queries and plan the search.
+ *
+ * Copies the queries and the scoring parameters to the device, chooses the
+ * kernel tiling for each query, and allocates all device scratch the search
+ * needs, so that sw_search_prepared allocates nothing and can be captured in
+ * a CUDA graph.  The profile tables of Sec. 8 (query profile P[c][i] =
+ * SM(Q[i], c)) are built on the device inside every sw_search_prepared call.
+ *
+ *   queries, q_offsets, n_queries   host pointers, same layout as the database
+ *   submat                          host pointer, 20x20 int8 (see above)
+ *   gap_open, gap_extend            see the gap convention above
+ *   mode                            SW_MODE_INT32 or SW_MODE_PACKED
+ *   cutover                         database sequences at least this long use
+ *                                   the intra-task (multi-warp) kernel; <= 0
+ *                                   selects the built-in default (2048)
+ *   stream                          upload stream; the call returns after it completes
+ *   out                             receives the new handle
+ *
+ * Errors: SW_EINVAL, SW_ENOMEM, SW_ECUDA.
+ */
+int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q_offsets,
+                       int64_t n_queries, const int8_t *submat, int32_t gap_open,
+                       int32_t gap_extend, int32_t mode, int32_t cutover, void *stream,
+                       sw_queries **out);
+
+/* Release a prepared query batch.  NULL is accepted. */
+int sw_queries_free(sw_queries *q);
+
+/*
+ * sw_search_prepared -- score every prepared query against the database.
+ *
+ * Device-only and asynchronous: enqueues profile construction, the
+ * dynamic-programming kernels, (packed mode) overflow detection and the exact
+ * int32 rescue, and the scatter to caller order on `stream`, then returns.
+ * No allocation and no host synchronisation happen inside.
+ *
+ *   scores_dev  DEVICE pointer, n_queries * n_db int32, written in caller order
+ *
+ * Errors: SW_EINVAL (null / mismatched handles, host pointer), SW_ECUDA.
+ * A bounded device wait that expires is reported by the next
+ * sw_queries_status call as SW_ETIMEOUT.
+ */
+int sw_search_prepared(const sw_db *db, const sw_queries *q, int32_t *scores_dev, void *stream);
+
+/*
+ * sw_queries_status -- read back the device status of the last search on q.
+ * Synchronises `stream`.  *rescued receives the number of (query, sequence)
+ * pairs whose packed score saturated and was recomputed in int32 (0 in int32
+ * mode).  Returns SW_ETIMEOUT if a bounded device wait expired.
+ */
+int sw_queries_status(const sw_queries *q, void *stream, int64_t *rescued);
+
+/*
+ * sw_search -- one-call search: prepare the queries, search, copy the scores
+ * out, release the batch.  scores_out may be a host or a device pointer
+ * (n_queries * n_db int32, caller order).  The call returns when the scores
+ * are in place.  Errors: as sw_queries_prepare / sw_search_prepared, plus
+ * SW_ETIMEOUT.
+ */
+int sw_search(const sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int64_t n_queries,
+              const int8_t *submat, int32_t gap_open, int32_t gap_extend, int32_t mode,
+              int32_t *scores_out, void *stream);
+
+/* Message for the last failed call on this thread ("" if none). */
+const char *sw_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SWGB_H */

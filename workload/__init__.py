@@ -1,0 +1,5 @@
+"""Seeded synthetic inputs (sequences, scoring data) shared by the oracle's
+tests, the GPU tests and the benchmark.  Input generation only."""
+
+from .matrices import ALPHABET, BLOSUM62, ROBINSON_FREQS, GAP_OPEN, GAP_EXTEND, encode, decode  # noqa: F401
+from .gen import Sequences, from_list, make_config, random_sequences, sample_indices, mutate  # noqa: F401

@@ -1,0 +1,205 @@
+"""Seeded synthetic protein workloads.
+
+These inputs stand in for the paper's protein benchmark (Env. NR 2021_04 as
+the database, 20 Swiss-Prot queries of 144-5478 residues, BLOSUM62, gaps
+10/2; Sec. 4.1), which is not available here.  Recipe:
+
+* sequence lengths: ``L = clip(round(exp(ln(median) + sigma * N(0,1))), lo, hi)``;
+* residues: i.i.d. draws from the Robinson & Robinson background law over the
+  20 standard amino acids (``workload.matrices.ROBINSON_FREQS``);
+* planted homologs: per position a substitution with probability ``p_sub`` (a
+  background draw different from the original) and an indel event with
+  probability ``p_indel`` (insertion or deletion with equal odds, length
+  ``Geometric(0.5)`` on 1, 2, ...);
+* every generator is driven by ``numpy.random.PCG64`` with a fixed seed.
+
+The module holds input generation only: no part of the alignment method.
+It is the one module that both the CPU oracle's tests and the GPU path use.
+"""
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from .matrices import ROBINSON_FREQS
+
+
+@dataclass
+class Sequences:
+    """A set of sequences as one concatenated uint8 code array plus offsets.
+
+    ``offsets`` has ``len + 1`` entries; sequence ``i`` is
+    ``residues[offsets[i]:offsets[i+1]]``.
+    """
+
+    residues: np.ndarray
+    offsets: np.ndarray
+
+    def __post_init__(self):
+        self.residues = np.ascontiguousarray(self.residues, dtype=np.uint8)
+        self.offsets = np.ascontiguousarray(self.offsets, dtype=np.int64)
+
+    def __len__(self):
+        return len(self.offsets) - 1
+
+    def __getitem__(self, i):
+        return self.residues[self.offsets[i]:self.offsets[i + 1]]
+
+    @property
+    def lengths(self):
+        return np.diff(self.offsets)
+
+    @property
+    def total(self):
+        return int(self.offsets[-1])
+
+    def subset(self, idx):
+        return from_list([self[int(i)] for i in idx])
+
+    def as_list(self):
+        return [self[i] for i in range(len(self))]
+
+
+def from_list(seqs):
+    seqs = [np.asarray(s, dtype=np.uint8) for s in seqs]
+    offsets = np.zeros(len(seqs) + 1, dtype=np.int64)
+    if seqs:
+        offsets[1:] = np.cumsum([len(s) for s in seqs])
+        res = np.concatenate(seqs) if offsets[-1] > 0 else np.zeros(0, np.uint8)
+    else:
+        res = np.zeros(0, np.uint8)
+    return Sequences(res, offsets)
+
+
+def lognormal_lengths(rng, n, median, sigma, lo, hi):
+    z = rng.standard_normal(n)
+    lengths = np.rint(np.exp(np.log(median) + sigma * z))
+    return np.clip(lengths, lo, hi).astype(np.int64)
+
+
+def random_residues(rng, total):
+    """``total`` i.i.d. residue codes from the background law."""
+    cdf = np.cumsum(ROBINSON_FREQS)
+    cdf /= cdf[-1]
+    out = np.empty(total, dtype=np.uint8)
+    step = 1 << 24
+    for s in range(0, total, step):
+        e = min(total, s + step)
+        out[s:e] = np.searchsorted(cdf, rng.random(e - s), side="right")
+    np.minimum(out, 19, out=out)
+    return out
+
+
+def random_sequences(seed, n, median, sigma, lo, hi):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lengths = lognormal_lengths(rng, n, median, sigma, lo, hi)
+    offsets = np.zeros(n + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum(lengths)
+    return Sequences(random_residues(rng, int(offsets[-1])), offsets)
+
+
+def random_sequence(rng, length):
+    return random_residues(rng, int(length))
+
+
+def mutate(rng, seq, p_sub=0.10, p_indel=0.01):
+    """A homolog of ``seq`` under the substitution + indel model above."""
+    cdf = np.cumsum(ROBINSON_FREQS)
+    cdf /= cdf[-1]
+    out = []
+    i = 0
+    n = len(seq)
+    while i < n:
+        if rng.random() < p_indel:
+            k = int(rng.geometric(0.5))
+            if rng.random() < 0.5:  # insertion of k background residues
+                out.extend(int(min(19, np.searchsorted(cdf, rng.random(), side="right"))) for _ in range(k))
+            else:  # deletion of k residues
+                i += k
+                continue
+        c = int(seq[i])
+        if rng.random() < p_sub:
+            while True:
+                r = int(min(19, np.searchsorted(cdf, rng.random(), side="right")))
+                if r != c:
+                    c = r
+                    break
+        out.append(c)
+        i += 1
+    return np.array(out, dtype=np.uint8)
+
+
+# ---------------------------------------------------------------------------
+# The five benchmark workloads.
+# ---------------------------------------------------------------------------
+
+DB_SEED = 1000
+QUERY_SEED = 2000
+ARRIVAL_SEED = 3000
+SAMPLE_SEED = 4000
+
+
+def config2_query_lengths():
+    """20 query lengths spread log-uniformly over 144..5478 residues."""
+    return [int(round(144 * (5478 / 144) ** (k / 19))) for k in range(20)]
+
+
+def make_config(k, n_db=None, n_queries=None):
+    """Build workload ``k`` (1..5).
+
+    Returns a dict with ``db`` (Sequences), ``queries`` (Sequences) and, where
+    the workload has them, ``homolog_ids`` (config 3) or ``arrivals`` (config 5,
+    seconds).  ``n_db`` / ``n_queries`` shrink the workload (tests only).
+    """
+    out = {"config": k}
+    if k in (1, 3):
+        db = random_sequences(DB_SEED + 1, n_db or 2000, 300, 0.5, 20, 1000)
+        rng = np.random.Generator(np.random.PCG64(QUERY_SEED + 1))
+        q144 = random_sequence(rng, 144)
+        if k == 1:
+            out.update(db=db, queries=from_list([q144]))
+            return out
+        rng3 = np.random.Generator(np.random.PCG64(QUERY_SEED + 3))
+        src = random_sequence(rng3, 8000)
+        n_hom = max(1, round(0.005 * len(db)))
+        homologs = [mutate(rng3, src) for _ in range(n_hom)]
+        seqs = db.as_list()
+        pos = np.sort(rng3.choice(len(seqs) + n_hom, size=n_hom, replace=False))
+        merged, hi, si = [], 0, 0
+        for p in range(len(seqs) + n_hom):
+            if hi < n_hom and pos[hi] == p:
+                merged.append(homologs[hi])
+                hi += 1
+            else:
+                merged.append(seqs[si])
+                si += 1
+        out.update(db=from_list(merged), queries=from_list([q144, src]), homolog_ids=pos.astype(np.int64))
+        return out
+    if k == 2:
+        db = random_sequences(DB_SEED + 2, n_db or 200_000, 300, 0.5, 20, 1000)
+        rng = np.random.Generator(np.random.PCG64(QUERY_SEED + 2))
+        lens = config2_query_lengths()
+        if n_queries:
+            lens = lens[:n_queries]
+        out.update(db=db, queries=from_list([random_sequence(rng, m) for m in lens]))
+        return out
+    if k == 4:
+        db = random_sequences(DB_SEED + 4, n_db or 50_000, 300, 0.5, 20, 1000)
+        q = random_sequences(QUERY_SEED + 4, n_queries or 1000, 350, 0.5, 50, 2000)
+        out.update(db=db, queries=q)
+        return out
+    if k == 5:
+        db = random_sequences(DB_SEED + 5, n_db or 500_000, 300, 0.65, 20, 1000)
+        nq = n_queries or 10_000
+        q = random_sequences(QUERY_SEED + 5, nq, 400, 0.5, 30, 3000)
+        rng = np.random.Generator(np.random.PCG64(ARRIVAL_SEED))
+        arrivals = np.cumsum(rng.exponential(1.0 / 50.0, size=nq))
+        out.update(db=db, queries=q, arrivals=arrivals)
+        return out
+    raise ValueError(f"unknown workload {k}")
+
+
+def sample_indices(n, k, seed=SAMPLE_SEED):
+    """A seeded sample of ``k`` distinct subject indices out of ``n`` (sorted)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.sort(rng.choice(n, size=min(k, n), replace=False)).astype(np.int64)
