@@ -1,0 +1,366 @@
+#!/usr/bin/env python3
+"""Benchmark: protein database search GCUPS on GB300 (Eq. 5: GCUPS = |Q| x |D| / (t x 1e9)).
+
+Workload (default): 20 synthetic queries of 144..5478 residues (log-uniform)
+against a 200,000-sequence synthetic database (~67.5M residues; log-normal
+lengths, median 300, clamped 20..1000; Robinson background residues),
+BLOSUM62, gaps 10 + 2k.  The synthetic inputs stand in for the paper's
+Swiss-Prot queries and Env. NR database (Sec. 4.1).
+
+One step = one full search of all queries against the resident database:
+profile build, packed s16x2 DP kernel, overflow rescue, scatter.  `value` is
+kernel-side GCUPS with inputs resident in HBM (device-side CUDA events,
+L2 flushed between steps); `e2e` is the same search through the one-call
+C-ABI entry point sw_search with host query and score buffers (copies
+inside the timed region).  The plain int32 kernel is timed on the same
+workload and reported beside it.
+
+--impl reference times the CPU oracle (scalar int32 Gotoh, threaded across
+pairs) on a bounded sample of the same workload on the host cores.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GCUPS per GB300, packed-int16/8 batched vs plain int32; p50/p99 query latency"
+WORKLOAD = "protein DB search: 20 queries (144-5478 aa) x 200,000 synthetic proteins (~67.5M aa), BLOSUM62, gaps 10+2k"
+SM_COUNT_FALLBACK = 152
+INT_LANES_PER_SM_CLK = 128  # issue-limited 32-bit integer lanes per SM per clock (4 SMSPs x 32)
+OPS_PER_CELL = {"packed": 6.0, "int32": 13.0}
+DP_KERNEL = "inter_kernel<16, packed>"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the int32 and small-config side measurements")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# distributed helpers (one process per GPU; weak scaling, no data-path collective)
+# ----------------------------------------------------------------------------
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg, device=None):
+    if pg is not None:
+        if device is not None:
+            pg.barrier(device_ids=[device])
+        else:
+            pg.barrier()
+
+
+def max_over_ranks(pg, x, device=None):
+    if pg is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=f"cuda:{device}" if device is not None else "cpu")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        under = [x for x in sm if smax and x > 0.5 * max(smax)] or sm
+        return {"sm_mhz": float(np.median(under)) if under else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def dp_kernel_traffic():
+    """DRAM bytes per launch of the DP kernel from the committed ncu summary,
+    or None if the kernel source changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "dp_kernel_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    src = os.path.join(ROOT, "paper_2412_08308_gb300", "csrc", "k_inter.cu")
+    sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    if rec.get("source_sha1") != sha:
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+# ----------------------------------------------------------------------------
+# the CPU oracle on a bounded sample (cpu_baseline and --impl reference)
+# ----------------------------------------------------------------------------
+
+def oracle_sample_gcups(w, n_subjects, seed=4000):
+    import oracle
+    from workload import sample_indices
+    from workload.matrices import BLOSUM62
+
+    oracle.build()
+    idx = sample_indices(len(w["db"]), n_subjects, seed=seed)
+    cells = float(w["queries"].total) * float(w["db"].lengths[idx].sum())
+    threads = oracle.default_threads()
+    t0 = time.perf_counter()
+    oracle.scores(w["queries"], w["db"], BLOSUM62, 10, 2, subset=idx, threads=threads)
+    dt = time.perf_counter() - t0
+    return cells / dt / 1e9, threads, cells, dt
+
+
+def run_reference(args, w):
+    world, rank, local, pg = dist_setup(args)
+    if rank != 0:
+        return
+    n_sub = 400
+    for _ in range(args.warmup):
+        oracle_sample_gcups(w, 50, seed=4100)
+    times, cells_total = [], 0.0
+    threads = 1
+    for s in range(args.steps):
+        g, threads, cells, dt = oracle_sample_gcups(w, n_sub, seed=4200 + s)
+        times.append(dt)
+        cells_total += cells
+    T = sum(times)
+    value = cells_total / T / 1e9
+    sample = f"all {len(w['queries'])} queries x {n_sub} seeded database sequences per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "GCUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * T / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": round(value, 3), "unit": "GCUPS", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+
+def time_prepared(pq, out, steps, flush, timing=False):
+    import torch
+
+    t_steps, k_steps = [], []
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        pq.search(out)
+        e.record()
+        torch.cuda.synchronize()
+        t_steps.append(s.elapsed_time(e) / 1e3)
+        if timing:
+            k_steps.append(pq.kernel_ms() / 1e3)
+    return t_steps, k_steps
+
+
+def run_ours(args, w):
+    import torch
+
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    from paper_2412_08308_gb300 import api, build
+    from workload.matrices import BLOSUM62
+
+    build()
+    q = w["queries"]
+    db_s = w["db"]
+    cells = float(q.total) * float(db_s.total)
+    db = api.Database.from_sequences(db_s)
+    pq = api.PreparedQueries(db, q.residues, q.offsets, BLOSUM62, 10, 2, "packed")
+    pq.set_timing(True)
+    out = torch.empty((len(q), len(db_s)), dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")  # > 129 MB L2
+
+    for _ in range(max(3, args.warmup)):
+        pq.search(out)
+    torch.cuda.synchronize()
+    rescued = pq.status()
+
+    clocks = Clocks(local)
+    barrier(pg, local)
+    torch.cuda.synchronize()
+    clocks.start()
+    t_steps, k_steps = time_prepared(pq, out, args.steps, flush, timing=True)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(pg, local)
+    T = max_over_ranks(pg, sum(t_steps), local)
+    value = world * cells * args.steps / T / 1e9
+    k_mean = float(np.mean(k_steps))
+    launches_per_step = 4  # profile build, packed DP, rescue-task build, int32 rescue DP
+
+    # roofline of the DP kernel: issue-limited integer lanes (alu)
+    peaks = measured_peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count or SM_COUNT_FALLBACK
+    peak_gops = n_sm * INT_LANES_PER_SM_CLK * sm_mhz * 1e6 / 1e9
+    achieved_gops = cells / k_mean / 1e9 * OPS_PER_CELL["packed"]
+    roofline = {"bound": "alu", "achieved": round(achieved_gops, 1), "peak": round(peak_gops, 1),
+                "unit": "Gop/s", "frac": round(achieved_gops / peak_gops, 4), "traffic": dp_kernel_traffic(),
+                "kernel": DP_KERNEL, "ops_per_cell": OPS_PER_CELL["packed"],
+                "peak_basis": f"{n_sm} SMs x {INT_LANES_PER_SM_CLK} int lanes/clk x {sm_mhz:.0f} MHz (sm_max_mhz of "
+                              "MEASURED_PEAKS.json)",
+                "kernel_gcups": round(cells / k_mean / 1e9, 1)}
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        # the plain int32 kernel (Algorithm 1 body) on the same workload
+        pq32 = api.PreparedQueries(db, q.residues, q.offsets, BLOSUM62, 10, 2, "int32")
+        pq32.search(out)
+        torch.cuda.synchronize()
+        t32, _ = time_prepared(pq32, out, max(1, min(3, args.steps)), flush)
+        extras["int32_gcups"] = round(cells * len(t32) / sum(t32) / 1e9, 1)
+        extras["packed_over_int32"] = round(value / world / extras["int32_gcups"], 3)
+        pq32.close()
+        # the small single-query workload (1 query of 144 aa x 2,000 proteins)
+        from workload import make_config
+
+        w1 = make_config(1)
+        db1 = api.Database.from_sequences(w1["db"])
+        c1 = float(w1["queries"].total) * float(w1["db"].total)
+        out1 = torch.empty((1, len(w1["db"])), dtype=torch.int32, device="cuda")
+        g1 = {}
+        for mode in ("packed", "int32"):
+            p1 = api.PreparedQueries(db1, w1["queries"].residues, w1["queries"].offsets, BLOSUM62, 10, 2, mode)
+            for _ in range(3):
+                p1.search(out1)
+            ts, _ = time_prepared(p1, out1, 10, flush)
+            g1[mode] = c1 / float(np.median(ts)) / 1e9
+            p1.close()
+        db1.close()
+        extras["config1_1x144_vs_2000"] = {"packed_gcups": round(g1["packed"], 1), "int32_gcups": round(g1["int32"], 1),
+                                           "ratio": round(g1["packed"] / g1["int32"], 3)}
+
+    # end to end through sw_search with host buffers
+    e2e = None
+    if not args.no_e2e:
+        h2d = pq.info()[0]
+        host_out = np.empty((len(q), len(db_s)), dtype=np.int32)
+        api.search(db, q.residues, q.offsets, BLOSUM62, 10, 2, "packed", out=host_out)
+        barrier(pg, local)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            api.search(db, q.residues, q.offsets, BLOSUM62, 10, 2, "packed", out=host_out)
+        torch.cuda.synchronize()
+        te = max_over_ranks(pg, time.perf_counter() - t0, local)
+        e2e = {"value": round(world * cells * args.steps / te / 1e9, 1), "unit": "GCUPS",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(host_out.nbytes)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        g, threads, c, dt = oracle_sample_gcups(w, 2000)
+        cpu = {"value": round(g, 3), "unit": "GCUPS", "cores": threads, "kind": "oracle",
+               "sample": f"all {len(q)} queries x 2,000 seeded database sequences ({c:.3g} cells, {dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": round(1e3 * T / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "s16x2+int32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "queries": len(q), "db_sequences": len(db_s), "db_residues": db_s.total,
+                       "cells_per_step": cells, "l2": "flushed between steps (256 MB write)",
+                       "parallelism": f"{world} GPU(s), independent full workload per GPU",
+                       "form": "packed s16x2 + exact int32 rescue", "rescued_pairs": rescued},
+            "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clk, "roofline": roofline,
+            "cpu_baseline": cpu,
+        }
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    pq.close()
+    db.close()
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def main():
+    args = parse()
+    from workload import make_config
+
+    w = make_config(args.config)
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

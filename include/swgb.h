@@ -93,8 +93,8 @@ int sw_db_stats(const sw_db *db, int64_t *n_seqs, int64_t *residues, int64_t *de
  * Copies the queries and the scoring parameters to the device, chooses the
  * kernel tiling for each query, and allocates all device scratch the search
  * needs, so that sw_search_prepared allocates nothing and can be captured in
- * a CUDA graph.  The profile tables of Sec. 8 (query profile P[c][i] =
- * SM(Q[i], c)) are built on the device inside every sw_search_prepared call.
+ * a CUDA graph.  The query profile (P[c][i] = SM(Q[i], c), the substitution
+ * term of Eq. 1 tabulated per residue) is built on the device in every search.
  *
  *   queries, q_offsets, n_queries   host pointers, same layout as the database
  *   submat                          host pointer, 20x20 int8 (see above)
@@ -139,6 +139,24 @@ int sw_search_prepared(const sw_db *db, const sw_queries *q, int32_t *scores_dev
  * mode).  Returns SW_ETIMEOUT if a bounded device wait expired.
  */
 int sw_queries_status(const sw_queries *q, void *stream, int64_t *rescued);
+
+/*
+ * sw_queries_set_timing -- when enable != 0, every later sw_search_prepared on
+ * q records CUDA events around its main dynamic-programming kernel (off by
+ * default, so that a search can be captured in a CUDA graph).
+ * sw_queries_kernel_ms -- synchronise `stream` and return in *ms the duration
+ * of that kernel in the last timed search.  Errors: SW_EINVAL if timing is off
+ * or no timed search ran, SW_ECUDA.
+ */
+int sw_queries_set_timing(sw_queries *q, int32_t enable);
+int sw_queries_kernel_ms(const sw_queries *q, void *stream, float *ms);
+
+/*
+ * sw_queries_info -- sizes of a prepared batch: bytes copied host->device by
+ * sw_queries_prepare (*h2d_bytes), device bytes it holds (*device_bytes) and
+ * the number of DP tasks of the main kernel (*n_tasks).  Any output may be NULL.
+ */
+int sw_queries_info(const sw_queries *q, int64_t *h2d_bytes, int64_t *device_bytes, int64_t *n_tasks);
 
 /*
  * sw_search -- one-call search: prepare the queries, search, copy the scores

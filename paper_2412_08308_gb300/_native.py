@@ -1,0 +1,129 @@
+"""ctypes binding of the C-ABI in include/swgb.h (argument marshalling only).
+
+Every function here has the name of the C entry point it wraps and forwards
+plain pointers and sizes; all work happens in libswgb.so.  There is no
+fallback: if the library is missing, importing the binding raises.
+"""
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libswgb.so")
+
+SW_OK, SW_EINVAL, SW_ENOMEM, SW_ECUDA, SW_ETIMEOUT = 0, 1, 2, 3, 4
+SW_MODE_INT32, SW_MODE_PACKED = 0, 1
+
+# every symbol include/swgb.h declares, with (restype, argtypes)
+_p, _i64, _i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+_pp = ctypes.POINTER(ctypes.c_void_p)
+_pi64 = ctypes.POINTER(ctypes.c_int64)
+SIGNATURES = {
+    "sw_db_prepare": (ctypes.c_int, [_p, _p, _i64, _p, _pp]),
+    "sw_db_free": (ctypes.c_int, [_p]),
+    "sw_db_stats": (ctypes.c_int, [_p, _pi64, _pi64, _pi64]),
+    "sw_queries_prepare": (ctypes.c_int, [_p, _p, _p, _i64, _p, _i32, _i32, _i32, _i32, _p, _pp]),
+    "sw_queries_free": (ctypes.c_int, [_p]),
+    "sw_search_prepared": (ctypes.c_int, [_p, _p, _p, _p]),
+    "sw_queries_status": (ctypes.c_int, [_p, _p, _pi64]),
+    "sw_search": (ctypes.c_int, [_p, _p, _p, _i64, _p, _i32, _i32, _i32, _p, _p]),
+    "sw_queries_set_timing": (ctypes.c_int, [_p, _i32]),
+    "sw_queries_kernel_ms": (ctypes.c_int, [_p, _p, ctypes.POINTER(ctypes.c_float)]),
+    "sw_queries_info": (ctypes.c_int, [_p, _pi64, _pi64, _pi64]),
+    "sw_last_error": (ctypes.c_char_p, []),
+}
+
+
+class SwError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"swgb error {code}: {msg}")
+        self.code = code
+
+
+def load(path=LIB_PATH):
+    if not os.path.exists(path):
+        raise RuntimeError(f"the CUDA library {path} is not built; run paper_2412_08308_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = load()
+    return _lib
+
+
+def check(rc):
+    if rc != SW_OK:
+        raise SwError(rc, lib().sw_last_error().decode())
+    return rc
+
+
+def sw_last_error():
+    return lib().sw_last_error().decode()
+
+
+def sw_db_prepare(residues_ptr, offsets_ptr, n_seqs, stream):
+    h = ctypes.c_void_p()
+    check(lib().sw_db_prepare(residues_ptr, offsets_ptr, n_seqs, stream, ctypes.byref(h)))
+    return h
+
+
+def sw_db_free(h):
+    return check(lib().sw_db_free(h))
+
+
+def sw_db_stats(h):
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    check(lib().sw_db_stats(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def sw_queries_prepare(db, q_ptr, qoff_ptr, n_queries, submat_ptr, gap_open, gap_extend, mode, cutover, stream):
+    h = ctypes.c_void_p()
+    check(lib().sw_queries_prepare(db, q_ptr, qoff_ptr, n_queries, submat_ptr, gap_open, gap_extend, mode,
+                                   cutover, stream, ctypes.byref(h)))
+    return h
+
+
+def sw_queries_free(h):
+    return check(lib().sw_queries_free(h))
+
+
+def sw_search_prepared(db, qh, scores_dev_ptr, stream):
+    return check(lib().sw_search_prepared(db, qh, scores_dev_ptr, stream))
+
+
+def sw_queries_status(qh, stream):
+    r = ctypes.c_int64()
+    check(lib().sw_queries_status(qh, stream, ctypes.byref(r)))
+    return r.value
+
+
+def sw_search(db, q_ptr, qoff_ptr, n_queries, submat_ptr, gap_open, gap_extend, mode, scores_ptr, stream):
+    return check(lib().sw_search(db, q_ptr, qoff_ptr, n_queries, submat_ptr, gap_open, gap_extend, mode,
+                                 scores_ptr, stream))
+
+
+def sw_queries_set_timing(qh, enable):
+    return check(lib().sw_queries_set_timing(qh, int(enable)))
+
+
+def sw_queries_kernel_ms(qh, stream):
+    v = ctypes.c_float()
+    check(lib().sw_queries_kernel_ms(qh, stream, ctypes.byref(v)))
+    return v.value
+
+
+def sw_queries_info(qh):
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    check(lib().sw_queries_info(qh, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value

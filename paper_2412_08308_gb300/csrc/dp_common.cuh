@@ -1,0 +1,202 @@
+// Cell arithmetic shared by the inter-task and intra-task kernels: one column
+// step of R query rows owned by one lane (Sec. 2.2 Eqs. 1-3).
+//
+// int32 form: Algorithm 1's statements, one cell per lane op.
+// packed form: two cells per 32-bit word.  Each 16-bit half holds the true
+// value plus a bias B >= Go + Ge + K, so every intermediate of a cell update
+// lies in [0, 32767] as long as the pair's score stays below 32767 - max(SM):
+// additions are plain 32-bit IADD/IADD3 (no carry or borrow crosses the
+// halves) and maxima are per-half VIMNMX (__vmaxs2), all full-rate on sm_103.
+#pragma once
+
+#include <cstdint>
+#include <type_traits>
+
+#include "internal.h"
+
+namespace swgb {
+
+constexpr uint32_t kPadPair = 20u | (20u << 16);
+
+struct Consts {
+  // packed
+  uint32_t goW, geW, bW, negKW, H0W, F0W, E0W;
+  // int32
+  int32_t go, ge, k;
+};
+
+__device__ __forceinline__ Consts make_consts(const Scoring &sc) {
+  Consts c;
+  c.goW = (uint32_t)sc.go * 0x10001u;
+  c.geW = (uint32_t)sc.ge * 0x10001u;
+  c.bW = (uint32_t)sc.bias * 0x10001u;
+  c.negKW = 0u - (uint32_t)sc.kbias * 0x10001u;
+  c.H0W = c.bW;
+  c.F0W = (uint32_t)(sc.bias - sc.go) * 0x10001u;
+  c.E0W = c.F0W;
+  c.go = sc.go;
+  c.ge = sc.ge;
+  c.k = sc.kbias;
+  return c;
+}
+
+// PTX prmt.b32 (default mode): each selector nibble picks one of the 8 bytes
+// {b, a}; a set nibble msb replicates the sign of the picked byte instead.
+// (CUDA's __byte_perm masks the nibbles to 3 bits, so it cannot express the
+// sign-replicate form used here.)
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+  uint32_t d;
+  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+  return d;
+}
+
+// Selectors: pair(i) -> (byte i of a, 0, byte i of b, 0) for bytes < 128 (the
+// sign of such a byte is 0); one(i) -> byte i of a, zero-extended from b = 0.
+__host__ __device__ constexpr uint32_t sel_pair(int i) {
+  return (uint32_t)i | ((uint32_t)(i | 8) << 4) | ((uint32_t)(4 + i) << 8) | ((uint32_t)((4 + i) | 8) << 12);
+}
+__host__ __device__ constexpr uint32_t sel_one(int i) { return 0x4440u | (uint32_t)i; }
+
+template <int R>
+__device__ __forceinline__ void load_prof(const uint8_t *p, uint32_t (&w)[R / 4]) {
+  static_assert(R % 4 == 0, "rows per lane must be a multiple of 4");
+  if constexpr (R % 16 == 0) {
+#pragma unroll
+    for (int i = 0; i < R / 16; ++i) {
+      const uint4 v = reinterpret_cast<const uint4 *>(p)[i];
+      w[4 * i + 0] = v.x; w[4 * i + 1] = v.y; w[4 * i + 2] = v.z; w[4 * i + 3] = v.w;
+    }
+  } else if constexpr (R % 8 == 0) {
+#pragma unroll
+    for (int i = 0; i < R / 8; ++i) {
+      const uint2 v = reinterpret_cast<const uint2 *>(p)[i];
+      w[2 * i + 0] = v.x; w[2 * i + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < R / 4; ++i) w[i] = reinterpret_cast<const uint32_t *>(p)[i];
+  }
+}
+
+__device__ __forceinline__ uint32_t word_of(const uint4 &v, int i) {
+  return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+}
+
+template <bool PACKED>
+using Word = typename std::conditional<PACKED, uint32_t, int32_t>::type;
+
+// Per-lane DP state of R rows.
+template <int R, bool PACKED>
+struct LaneState {
+  Word<PACKED> Hl[R];  // H of each row at the previous column
+  Word<PACKED> E[R];   // packed: E of each row at the current column; int32: E at the previous column
+  Word<PACKED> hdiag;  // H of the row above this lane's first row, previous column
+};
+
+template <int R, bool PACKED>
+__device__ __forceinline__ void lane_reset(LaneState<R, PACKED> &st, const Consts &cs) {
+  using W = Word<PACKED>;
+  const W H0 = PACKED ? (W)cs.H0W : (W)0;
+  const W E0 = PACKED ? (W)cs.E0W : (W)0;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    st.Hl[r] = H0;
+    st.E[r] = E0;
+  }
+  st.hdiag = H0;
+}
+
+// One column: inputs are the (H, F) pair passed down from the row above this
+// lane's rows and the residue code(s) of the column; prow points at this
+// lane's R profile bytes of residue row 0 (rows are `stride` bytes apart).
+// Outputs the (H, F) pair for the row below: int32 passes (H, F) of the last
+// row; packed passes (H of the last row, F of the row below it).
+template <int R, bool PACKED>
+__device__ __forceinline__ void column_step(LaneState<R, PACKED> &st, const uint8_t *prow, int stride,
+                                            uint32_t res, Word<PACKED> inH, Word<PACKED> inF, const Consts &cs,
+                                            Word<PACKED> &S, Word<PACKED> &outH, Word<PACKED> &outF) {
+  using W = Word<PACKED>;
+  uint32_t pa[R / 4];
+  load_prof<R>(prow + (res & 0xffu) * stride, pa);
+  if constexpr (PACKED) {
+    uint32_t pb[R / 4];
+    load_prof<R>(prow + (res >> 16) * stride, pb);
+    uint32_t hd = (uint32_t)st.hdiag, f = (uint32_t)inF;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const uint32_t p = prmt(pa[r >> 2], pb[r >> 2], sel_pair(r & 3));
+      const uint32_t x = hd + p + cs.negKW;
+      uint32_t tt = __vmaxs2(x, (uint32_t)st.E[r]);
+      tt = __vmaxs2(tt, cs.bW);
+      const uint32_t h = __vmaxs2(tt, f);
+      S = (W)__vmaxs2((uint32_t)S, h);
+      const uint32_t hgo = h - cs.goW;
+      st.E[r] = (W)__vmaxs2((uint32_t)st.E[r] - cs.geW, hgo);
+      f = __vmaxs2(f - cs.geW, hgo);
+      hd = (uint32_t)st.Hl[r];
+      st.Hl[r] = (W)h;
+    }
+    outH = st.Hl[R - 1];
+    outF = (W)f;
+  } else {
+    // Algorithm 1, statement by statement.
+    int32_t hul = (int32_t)st.hdiag, hu = (int32_t)inH, fu = (int32_t)inF;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int32_t sm = (int32_t)prmt(pa[r >> 2], 0u, sel_one(r & 3)) - cs.k;
+      const int32_t e1 = (int32_t)st.E[r] - cs.ge;
+      const int32_t e2 = (int32_t)st.Hl[r] - cs.go;
+      const int32_t e = max(e1, e2);
+      const int32_t f1 = fu - cs.ge;
+      const int32_t f2 = hu - cs.go;
+      const int32_t f = max(f1, f2);
+      int32_t h = hul + sm;
+      h = max(h, e);
+      h = max(h, f);
+      h = max(h, 0);
+      S = (W)max((int32_t)S, h);
+      hul = (int32_t)st.Hl[r];
+      st.Hl[r] = (W)h;
+      st.E[r] = (W)e;
+      hu = h;
+      fu = f;
+    }
+    outH = (W)hu;
+    outF = (W)fu;
+  }
+  st.hdiag = inH;
+}
+
+template <bool PACKED>
+__device__ __forceinline__ Word<PACKED> score_max(Word<PACKED> a, Word<PACKED> b) {
+  if constexpr (PACKED) return (Word<PACKED>)__vmaxs2((uint32_t)a, (uint32_t)b);
+  else return max(a, b);
+}
+
+// Epilogue for one database unit: un-bias, flag possible overflows (packed)
+// and scatter to caller order.
+template <bool PACKED>
+__device__ __forceinline__ void write_scores(Word<PACKED> S, int posA, int posB, int q, const DbView &db,
+                                             const Scoring &sc, int32_t *out, int64_t out_stride,
+                                             int32_t *flag_count, int32_t *flag_pos) {
+  const int64_t row = (int64_t)q * out_stride;
+  if constexpr (PACKED) {
+    const int32_t sa = (int32_t)((uint32_t)S & 0xffffu), sb = (int32_t)((uint32_t)S >> 16);
+    if (sa > sc.thresh) {
+      const int i = atomicAdd(&flag_count[q], 1);
+      flag_pos[row + i] = posA;
+    }
+    out[row + db.perm[posA]] = sa - sc.bias;
+    if (posB != posA) {
+      if (sb > sc.thresh) {
+        const int i = atomicAdd(&flag_count[q], 1);
+        flag_pos[row + i] = posB;
+      }
+      out[row + db.perm[posB]] = sb - sc.bias;
+    }
+  } else {
+    out[row + db.perm[posA]] = (int32_t)S;
+  }
+}
+
+}  // namespace swgb

@@ -1,0 +1,94 @@
+// Internal declarations shared by the host API (api.cu) and the kernel
+// translation units.  Not part of the public interface.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace swgb {
+
+constexpr int kAlphabet = 20;      // residue codes 0..19
+constexpr int kPadCode = 20;       // pad residue: profile row of the most negative score
+constexpr int kProfRows = 21;      // profile rows: 20 residues + pad
+constexpr int kColBlock = 16;      // columns per unrolled block / residue vector
+constexpr int kMinPad = 48;        // minimum padded database length (>= max lanes per chain + 16)
+constexpr int kMaxLanesPerChain = 32;
+
+// Scoring constants, derived once per query batch on the host.
+struct Scoring {
+  int32_t go;      // Go of Eqs. 2-3 = gap_open + gap_extend
+  int32_t ge;      // Ge of Eqs. 2-3 = gap_extend
+  int32_t kbias;   // K: profile bytes hold SM + K >= 0 (pad row holds 0)
+  int32_t maxp;    // max(0, max SM)
+  int32_t bias;    // B: packed 16-bit lanes hold true value + B
+  int32_t thresh;  // packed lane overflows are possible only if stored S > thresh
+};
+
+// Per-query descriptor for the dynamic-programming kernels.
+struct QDesc {
+  int32_t m;         // query length
+  int32_t L;         // lanes per chain (1..32)
+  int32_t R;         // rows per lane
+  int32_t nchunks;   // ceil(m / (L*R)) (>= 1)
+  int32_t chunk_bytes;  // bytes of one profile chunk = 21 * chunk_stride
+  int32_t chunk_stride; // bytes per profile row within a chunk (>= L*R, multiple of 16)
+  int64_t prof_off;  // byte offset of chunk 0 in the profile buffer
+  int64_t qoff;      // offset of the query residues in the query residue buffer
+};
+
+// A unit of DP work for one chain: one database sequence (int32 form) or
+// two (packed form), given as positions in the length-sorted database.
+struct Task {
+  int32_t q;           // query index
+  int32_t unit_begin;  // first unit of the tile
+  int32_t unit_count;  // units in the tile (<= chains per CTA)
+  int32_t pad_;
+};
+
+struct DbView {
+  const uint8_t *res;   // packed residues, sorted order
+  const int64_t *off;   // [n] byte offset of sorted sequence k (16-byte aligned)
+  const int32_t *npad;  // [n] padded length (multiple of 16, >= kMinPad)
+  const int32_t *len;   // [n] true length
+  const int32_t *perm;  // [n] sorted position -> caller index
+  int64_t n;
+};
+
+struct InterArgs {
+  DbView db;
+  const int32_t *unit_pos;  // packed: 2 sorted positions per unit; int32: 1 per unit
+  const QDesc *qd;
+  const Task *tasks;
+  const int32_t *n_tasks;   // device word: number of tasks
+  int32_t *task_counter;    // device word, zeroed before launch
+  const uint8_t *prof;      // profile chunks (see QDesc)
+  int32_t pbuf_bytes;       // shared-memory bytes per profile buffer (>= every chunk_bytes)
+  uint2 *gbuf;              // chunk boundary scratch, per (CTA, chain slot): gbuf_stride entries
+  int32_t gbuf_stride;
+  int32_t *out;             // [nq][out_stride] scores in caller order
+  int64_t out_stride;
+  int32_t *flag_count;      // packed: [nq] number of flagged sequences per query
+  int32_t *flag_pos;        // packed: [nq][out_stride] flagged sorted positions
+  Scoring sc;
+  int32_t *status;          // device status word (SW_ETIMEOUT on an expired wait)
+};
+
+// launchers (k_inter.cu)
+int inter_threads();
+int inter_chains_per_cta(int L);
+bool inter_supported_R(int R);
+size_t inter_smem_bytes(int pbuf_bytes, int threads);
+cudaError_t launch_inter(const InterArgs &a, int R, bool packed, int grid, int threads, size_t smem,
+                         cudaStream_t s);
+int inter_max_ctas_per_sm(int R, bool packed, int threads, size_t smem);
+
+// support kernels (k_support.cu)
+cudaError_t launch_build_profiles(const uint8_t *qres, const QDesc *qd, int32_t nq, const int8_t *submat,
+                                  int32_t kbias, uint8_t *prof, cudaStream_t s);
+// Build rescue tasks (one tile of <= chains-per-CTA flagged sequences per task) from the per-query
+// flag counts; writes the task count to *n_tasks.
+cudaError_t launch_rescue_tasks(const int32_t *flag_count, const QDesc *qd, int32_t nq, int64_t stride,
+                                int32_t chains_mult, Task *tasks, int32_t *n_tasks, int32_t *counter,
+                                cudaStream_t s);
+
+}  // namespace swgb

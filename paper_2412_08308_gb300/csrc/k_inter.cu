@@ -1,0 +1,279 @@
+// Inter-task Smith-Waterman/Gotoh kernels (Sec. 2.2 Eqs. 1-3; Sec. 3.1 "short
+// kernel"; Fig. 1 inter-sequence parallelism), re-designed for sm_103a.
+//
+// Work decomposition
+// ------------------
+// A *chain* of L lanes (4 <= L <= 32, several chains per warp) computes the
+// alignment matrix of one query against one database sequence (int32 form)
+// or against two sequences at once (packed form: two 16-bit cells per 32-bit
+// register).  Lane k of a chain owns R consecutive query rows of the current
+// *chunk* of L*R rows and sweeps the database columns; lane k works on column
+// t-k at step t, receiving the bottom row (H, F) of lane k-1 and the residue
+// code(s) through warp shuffles.  This is an anti-diagonal wavefront inside a
+// warp: cells on one anti-diagonal of lanes run in the same step.
+//
+// The query is processed chunk by chunk.  All chains of a CTA work on the same
+// query and move from chunk to chunk together: the profile slice of the next
+// chunk is staged into shared memory by a 1-D bulk TMA copy while the current
+// one is used, and the bottom boundary row of a chunk goes through a global
+// scratch strip to lane 0 of the same chain in the next chunk (prefetched with
+// cp.async into a small per-chain shared-memory ring).
+//
+// Persistent CTAs pull (query, tile of database units) tasks from an atomic
+// counter; tasks are ordered longest first.
+//
+// Cell arithmetic
+// ---------------
+// int32 form: the twelve-instruction body of Algorithm 1, one cell per lane op.
+// packed form: two cells per 32-bit word, each 16-bit half holding the true
+// value plus a bias B (B >= Go + Ge + K) so every intermediate stays in
+// [0, 32767]; additions are plain 32-bit IADD/IADD3 (no carry or borrow can
+// cross the halves) and maxima are full-rate per-half VIMNMX (__vmaxs2).  A
+// half whose final stored score exceeds 32767 - max(SM) may have overflowed;
+// it is flagged and recomputed exactly in int32 (rescue pass).
+#include "devutil.cuh"
+#include "dp_common.cuh"
+#include "internal.h"
+#include "../../include/swgb.h"
+
+namespace swgb {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kChainsPerWarpMax = 8;  // lanes per chain >= 4
+constexpr int kRingBytes = 320;       // residues: 2 slots x 2 seqs x 16 B; boundary: 2 slots x 16 x 8 B
+
+// One pass of a chain over all columns of its unit for the rows of one chunk.
+template <int R, bool PACKED>
+__device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, const int stride, const int L,
+                                           const int k, const int lane, const bool live, const int nblk,
+                                           const int npad, const int npa, const int npb,
+                                           const uint8_t *__restrict__ resA, const uint8_t *__restrict__ resB,
+                                           uint8_t *ring, uint2 *gb, const bool prev, const bool next,
+                                           const Consts &cs, Word<PACKED> &S) {
+  using W = Word<PACKED>;
+  const W H0 = PACKED ? (W)cs.H0W : (W)0;
+  const W F0 = PACKED ? (W)cs.F0W : (W)0;
+  LaneState<R, PACKED> st;
+  lane_reset(st, cs);
+  W outH = H0, outF = F0;
+  uint32_t outRes = kPadPair;
+  const int src = (k > 0) ? lane - 1 : lane;
+  const bool lead = live && k == 0;
+  const bool tail = live && (k == L - 1) && next;
+  uint8_t *rres = ring;                                  // [slot][seq][16 B]
+  uint2 *rgb = reinterpret_cast<uint2 *>(ring + 64);     // [slot][16]
+  const uint8_t *prow = pch + k * R;
+
+  auto prefetch = [&](int blk) {
+    const int slot = blk & 1;
+    const int col = blk * kColBlock;
+    uint8_t *d = rres + slot * 32;
+    if (col < npa) cp_async16(d, resA + col);
+    else *reinterpret_cast<uint4 *>(d) = make_uint4(0x14141414u, 0x14141414u, 0x14141414u, 0x14141414u);
+    if (PACKED) {
+      if (col < npb) cp_async16(d + 16, resB + col);
+      else *reinterpret_cast<uint4 *>(d + 16) = make_uint4(0x14141414u, 0x14141414u, 0x14141414u, 0x14141414u);
+    }
+    if (prev && col < npad) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) cp_async16(rgb + slot * 16 + 2 * i, gb + col + 2 * i);
+    }
+    cp_async_commit();
+  };
+  if (lead) {
+    prefetch(0);
+    prefetch(1);
+  }
+
+  for (int blk = 0; blk < nblk; ++blk) {
+    uint4 ra4 = make_uint4(0, 0, 0, 0), rb4 = make_uint4(0, 0, 0, 0);
+    if (lead) {
+      cp_async_wait<1>();
+      ra4 = *reinterpret_cast<const uint4 *>(rres + (blk & 1) * 32);
+      if (PACKED) rb4 = *reinterpret_cast<const uint4 *>(rres + (blk & 1) * 32 + 16);
+    }
+    const uint2 *gslot = rgb + (blk & 1) * 16;
+#pragma unroll
+    for (int s = 0; s < kColBlock; ++s) {
+      const int t = blk * kColBlock + s;
+      W inH = (W)__shfl_sync(0xffffffffu, outH, src);
+      W inF = (W)__shfl_sync(0xffffffffu, outF, src);
+      uint32_t inRes = __shfl_sync(0xffffffffu, outRes, src);
+      if (k == 0) {
+        const bool real = t < npad;
+        const uint32_t wa = word_of(ra4, s >> 2);
+        const uint32_t rr = PACKED ? prmt(wa, word_of(rb4, s >> 2), sel_pair(s & 3))
+                                   : prmt(wa, 0u, sel_one(s & 3));
+        inRes = real ? rr : kPadPair;
+        if (prev && real) {
+          const uint2 v = gslot[s];
+          inH = (W)v.x;
+          inF = (W)v.y;
+        } else {
+          inH = H0;
+          inF = F0;
+        }
+      }
+      column_step<R, PACKED>(st, prow, stride, inRes, inH, inF, cs, S, outH, outF);
+      outRes = inRes;
+      if (tail) {
+        const int j = t - (L - 1);
+        if (j >= 0 && j < npad) gb[j] = make_uint2((uint32_t)outH, (uint32_t)outF);
+      }
+    }
+    if (lead) {
+      if (blk + 2 < nblk) prefetch(blk + 2);
+      else cp_async_commit();
+    }
+  }
+  if (lead) cp_async_wait<0>();
+}
+
+template <int R, bool PACKED>
+__global__ void __launch_bounds__(kThreads, 2) inter_kernel(const InterArgs a) {
+  using W = Word<PACKED>;
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
+  volatile int *s_task = reinterpret_cast<volatile int *>(smem + 16);
+  uint8_t *pbuf = smem + 128;
+  uint8_t *rings = pbuf + 2 * a.pbuf_bytes;
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  const Consts cs = make_consts(a.sc);
+
+  if (threadIdx.x == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t par0 = 0u, par1 = 0u;
+  const int n_tasks = *a.n_tasks;
+
+  for (;;) {
+    if (threadIdx.x == 0) *s_task = atomicAdd(a.task_counter, 1);
+    __syncthreads();
+    const int t = *s_task;
+    if (t >= n_tasks) break;
+
+    const Task tk = a.tasks[t];
+    const QDesc qd = a.qd[tk.q];
+    const int L = qd.L;
+    const int G = 32 / L;
+    const int cw = lane / L;
+    const int k = lane - cw * L;
+    const int ci = warp * G + cw;
+    const bool live = (cw < G) && (ci < tk.unit_count);
+    int posA = 0, posB = 0, npa = 0, npb = 0;
+    if (live) {
+      const int u = tk.unit_begin + ci;
+      posA = a.unit_pos[PACKED ? 2 * u : u];
+      posB = PACKED ? a.unit_pos[2 * u + 1] : posA;
+      npa = a.db.npad[posA];
+      npb = PACKED ? a.db.npad[posB] : 0;
+    }
+    const int npad = max(npa, npb);
+    const int nblk = __reduce_max_sync(0xffffffffu, live ? (npad + L - 1 + kColBlock - 1) / kColBlock : 0);
+    const uint8_t *resA = a.db.res + (live ? a.db.off[posA] : 0);
+    const uint8_t *resB = a.db.res + (live ? a.db.off[posB] : 0);
+    const int cslot = warp * kChainsPerWarpMax + min(cw, kChainsPerWarpMax - 1);
+    uint8_t *ring = rings + cslot * kRingBytes;
+    uint2 *gb = a.gbuf + ((size_t)blockIdx.x * nwarps * kChainsPerWarpMax + cslot) * (size_t)a.gbuf_stride;
+
+    auto issue = [&](int c) {
+      const int b = c & 1;
+      mbar_arrive_expect_tx(&mbar[b], (uint32_t)qd.chunk_bytes);
+      bulk_g2s(pbuf + b * a.pbuf_bytes, a.prof + qd.prof_off + (int64_t)c * qd.chunk_bytes,
+               (uint32_t)qd.chunk_bytes, &mbar[b]);
+    };
+    if (threadIdx.x == 0) {
+      issue(0);
+      if (qd.nchunks > 1) issue(1);
+    }
+
+    W S = PACKED ? (W)cs.bW : (W)0;
+    for (int c = 0; c < qd.nchunks; ++c) {
+      const int b = c & 1;
+      const bool ok = mbar_wait_bounded(&mbar[b], b ? par1 : par0);
+      if (b) par1 ^= 1u;
+      else par0 ^= 1u;
+      if (!__syncthreads_and(ok)) {
+        if (threadIdx.x == 0) atomicExch(a.status, SW_ETIMEOUT);
+        return;
+      }
+      chain_pass<R, PACKED>(pbuf + b * a.pbuf_bytes, qd.chunk_stride, L, k, lane, live, nblk, npad, npa, npb,
+                            resA, resB, ring, gb, c > 0, c + 1 < qd.nchunks, cs, S);
+      __syncthreads();
+      if (threadIdx.x == 0 && c + 2 < qd.nchunks) issue(c + 2);
+    }
+
+    // max over the chain's lanes
+    for (int d = 1; d < L; d <<= 1) S = score_max<PACKED>(S, (W)__shfl_sync(0xffffffffu, S, (k + d < L) ? lane + d : lane));
+    if (live && k == 0)
+      write_scores<PACKED>(S, posA, posB, tk.q, a.db, a.sc, a.out, a.out_stride, a.flag_count, a.flag_pos);
+  }
+}
+
+template <int R, bool PACKED>
+cudaError_t launch_one(const InterArgs &a, int grid, int threads, size_t smem, cudaStream_t s) {
+  auto kern = inter_kernel<R, PACKED>;
+  static bool configured = false;  // per instantiation; max dynamic smem of this library is < 200 KB
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  kern<<<grid, threads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int R, bool PACKED>
+int occupancy_one(int threads, size_t smem) {
+  int n = 0;
+  auto kern = inter_kernel<R, PACKED>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem) != cudaSuccess) return 1;
+  return n > 0 ? n : 1;
+}
+
+}  // namespace
+
+int inter_threads() { return kThreads; }
+int inter_chains_per_cta(int L) { return (kThreads / 32) * (32 / L); }
+int inter_ring_bytes() { return kRingBytes; }
+int inter_chains_per_warp_slots() { return kChainsPerWarpMax; }
+
+size_t inter_smem_bytes(int pbuf_bytes, int threads) {
+  return 128 + 2 * (size_t)pbuf_bytes + (size_t)(threads / 32) * kChainsPerWarpMax * kRingBytes;
+}
+
+#define SWGB_INTER_R_LIST(X) X(8) X(12) X(16) X(24)
+
+bool inter_supported_R(int R) {
+#define SWGB_CASE(RR) if (R == RR) return true;
+  SWGB_INTER_R_LIST(SWGB_CASE)
+#undef SWGB_CASE
+  return false;
+}
+
+cudaError_t launch_inter(const InterArgs &a, int R, bool packed, int grid, int threads, size_t smem,
+                         cudaStream_t s) {
+#define SWGB_CASE(RR)                                                        \
+  if (R == RR) return packed ? launch_one<RR, true>(a, grid, threads, smem, s) \
+                             : launch_one<RR, false>(a, grid, threads, smem, s);
+  SWGB_INTER_R_LIST(SWGB_CASE)
+#undef SWGB_CASE
+  return cudaErrorInvalidValue;
+}
+
+int inter_max_ctas_per_sm(int R, bool packed, int threads, size_t smem) {
+#define SWGB_CASE(RR) \
+  if (R == RR) return packed ? occupancy_one<RR, true>(threads, smem) : occupancy_one<RR, false>(threads, smem);
+  SWGB_INTER_R_LIST(SWGB_CASE)
+#undef SWGB_CASE
+  return 1;
+}
+
+}  // namespace swgb
