@@ -36,9 +36,15 @@ sys.path.insert(0, ROOT)
 METRIC = "GCUPS per GB300, packed-int16/8 batched vs plain int32; p50/p99 query latency"
 WORKLOAD = "protein DB search: 20 queries (144-5478 aa) x 200,000 synthetic proteins (~67.5M aa), BLOSUM62, gaps 10+2k"
 SM_COUNT_FALLBACK = 152
-INT_LANES_PER_SM_CLK = 128  # issue-limited 32-bit integer lanes per SM per clock (4 SMSPs x 32)
-OPS_PER_CELL = {"packed": 6.0, "int32": 13.0}
-DP_KERNEL = "inter_kernel<16, packed>"
+# The integer ALU pipe of an sm_103 SMSP accepts one warp instruction every
+# second cycle (ncu: a stream of IMNMX / VIMNMX / IADD / PRMT runs the ALU pipe
+# at ~99% with issue at ~51%), i.e. 64 lanes per clock per SM.  Every max of
+# the recurrences runs there; the DP kernels are bound by it.
+ALU_LANES_PER_SM_CLK = 64
+# essential ALU-pipe (max) operations per cell: packed s16x2 = 5 per 32-bit
+# word of two cells (max with the zero floor, H, S, E, F); int32 = the 6 max
+# statements of Algorithm 1
+ALU_OPS_PER_CELL = {"packed": 2.5, "int32": 6.0}
 
 
 def parse():
@@ -51,6 +57,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the int32 and small-config side measurements")
+    ap.add_argument("--serve-requests", type=int, default=600,
+                    help="requests of the serving run (Poisson 50/s, 500,000-protein database); 0 skips it")
+    ap.add_argument("--mode", default="packed", choices=["packed", "int32"], help="form of the timed search")
+    ap.add_argument("--queries", type=int, default=0, help="use only the first K queries (profiling runs)")
+    ap.add_argument("--db-limit", type=int, default=0, help="use only the first N database sequences (profiling runs)")
     return ap.parse_args()
 
 
@@ -232,6 +243,52 @@ def time_prepared(pq, out, steps, flush, timing=False):
     return t_steps, k_steps
 
 
+def run_serving(n_requests, mode):
+    """Continuous-batching serving run on the config-5 shape: 500,000 synthetic
+    proteins (~180M residues) resident in HBM, queries (median 400, 30-3000)
+    arriving as a Poisson process at 50/s.  Reports latency percentiles and
+    offered vs sustained GCUPS over the first n_requests arrivals."""
+    import threading
+
+    from paper_2412_08308_gb300 import api
+    from paper_2412_08308_gb300.serve import Server
+    from workload import make_config
+    from workload.matrices import BLOSUM62
+
+    w = make_config(5, n_queries=n_requests)
+    db = api.Database.from_sequences(w["db"])
+    q = w["queries"]
+    arrivals = w["arrivals"]
+    srv = Server(db, BLOSUM62, 10, 2, mode, max_batch=8, n_streams=3)
+    t0 = time.perf_counter()
+    futs = []
+
+    def client():
+        for i in range(len(q)):
+            delay = t0 + arrivals[i] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            futs.append(srv.submit(q[i], arrival=t0 + arrivals[i]))
+
+    th = threading.Thread(target=client)
+    th.start()
+    th.join()
+    for f in futs:
+        f.result()
+    t_end = time.perf_counter()
+    srv.close()
+    st = srv.latency_stats()
+    cells = float(q.total) * float(w["db"].total)
+    span = t_end - t0
+    st.update({"workload": f"{len(q)} Poisson(50/s) queries (median 400 aa) x {len(w['db'])} proteins "
+                           f"({w['db'].total} aa)",
+               "offered_gcups": round(cells / float(arrivals[-1]) / 1e9, 1),
+               "sustained_gcups": round(cells / span / 1e9, 1), "wall_s": round(span, 2),
+               "batching": "continuous: up to 8 queries per batch, 3 batches in flight on separate streams"})
+    db.close()
+    return st
+
+
 def run_ours(args, w):
     import torch
 
@@ -245,7 +302,7 @@ def run_ours(args, w):
     db_s = w["db"]
     cells = float(q.total) * float(db_s.total)
     db = api.Database.from_sequences(db_s)
-    pq = api.PreparedQueries(db, q.residues, q.offsets, BLOSUM62, 10, 2, "packed")
+    pq = api.PreparedQueries(db, q.residues, q.offsets, BLOSUM62, 10, 2, args.mode)
     pq.set_timing(True)
     out = torch.empty((len(q), len(db_s)), dtype=torch.int32, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")  # > 129 MB L2
@@ -266,19 +323,19 @@ def run_ours(args, w):
     T = max_over_ranks(pg, sum(t_steps), local)
     value = world * cells * args.steps / T / 1e9
     k_mean = float(np.mean(k_steps))
-    launches_per_step = 4  # profile build, packed DP, rescue-task build, int32 rescue DP
+    launches_per_step = pq.info()[3]
 
-    # roofline of the DP kernel: issue-limited integer lanes (alu)
+    # roofline of the DP kernel: the integer ALU pipe (alu)
     peaks = measured_peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count or SM_COUNT_FALLBACK
-    peak_gops = n_sm * INT_LANES_PER_SM_CLK * sm_mhz * 1e6 / 1e9
-    achieved_gops = cells / k_mean / 1e9 * OPS_PER_CELL["packed"]
+    peak_gops = n_sm * ALU_LANES_PER_SM_CLK * sm_mhz * 1e6 / 1e9
+    achieved_gops = cells / k_mean / 1e9 * ALU_OPS_PER_CELL[args.mode]
     roofline = {"bound": "alu", "achieved": round(achieved_gops, 1), "peak": round(peak_gops, 1),
                 "unit": "Gop/s", "frac": round(achieved_gops / peak_gops, 4), "traffic": dp_kernel_traffic(),
-                "kernel": DP_KERNEL, "ops_per_cell": OPS_PER_CELL["packed"],
-                "peak_basis": f"{n_sm} SMs x {INT_LANES_PER_SM_CLK} int lanes/clk x {sm_mhz:.0f} MHz (sm_max_mhz of "
-                              "MEASURED_PEAKS.json)",
+                "kernel": "inter_kernel<R, %s>" % args.mode, "alu_ops_per_cell": ALU_OPS_PER_CELL[args.mode],
+                "peak_basis": f"{n_sm} SMs x {ALU_LANES_PER_SM_CLK} ALU-pipe lanes/clk x {sm_mhz:.0f} MHz "
+                              "(sm_max_mhz of MEASURED_PEAKS.json)",
                 "kernel_gcups": round(cells / k_mean / 1e9, 1)}
 
     extras = {}
@@ -315,15 +372,19 @@ def run_ours(args, w):
     if not args.no_e2e:
         h2d = pq.info()[0]
         host_out = np.empty((len(q), len(db_s)), dtype=np.int32)
-        api.search(db, q.residues, q.offsets, BLOSUM62, 10, 2, "packed", out=host_out)
+        api.search(db, q.residues, q.offsets, BLOSUM62, 10, 2, args.mode, out=host_out)
         barrier(pg, local)
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            api.search(db, q.residues, q.offsets, BLOSUM62, 10, 2, "packed", out=host_out)
+            api.search(db, q.residues, q.offsets, BLOSUM62, 10, 2, args.mode, out=host_out)
         torch.cuda.synchronize()
         te = max_over_ranks(pg, time.perf_counter() - t0, local)
         e2e = {"value": round(world * cells * args.steps / te / 1e9, 1), "unit": "GCUPS",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(host_out.nbytes)}
+
+    serving = None
+    if rank == 0 and args.serve_requests > 0 and not (args.queries or args.db_limit):
+        serving = run_serving(args.serve_requests, args.mode)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -332,16 +393,20 @@ def run_ours(args, w):
                "sample": f"all {len(q)} queries x 2,000 seeded database sequences ({c:.3g} cells, {dt:.1f} s)"}
 
     if rank == 0:
+        wl = WORKLOAD if not (args.queries or args.db_limit) else (
+            f"reduced profiling case: {len(q)} queries x {len(db_s)} synthetic proteins")
         line = {
             "metric": METRIC, "value": round(value, 1), "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": round(1e3 * T / args.steps, 3), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "s16x2+int32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "queries": len(q), "db_sequences": len(db_s), "db_residues": db_s.total,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "s16x2+int32" if args.mode == "packed" else "int32", "data": "synthetic",
+            "config": {"workload": wl, "queries": len(q), "db_sequences": len(db_s), "db_residues": db_s.total,
                        "cells_per_step": cells, "l2": "flushed between steps (256 MB write)",
                        "parallelism": f"{world} GPU(s), independent full workload per GPU",
-                       "form": "packed s16x2 + exact int32 rescue", "rescued_pairs": rescued},
+                       "form": "packed s16x2 + exact int32 rescue" if args.mode == "packed" else "plain int32 (Algorithm 1)",
+                       "rescued_pairs": rescued},
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clk, "roofline": roofline,
-            "cpu_baseline": cpu,
+            "cpu_baseline": cpu, "serving": serving,
         }
         line.update(extras)
         print(json.dumps(line), flush=True)
@@ -356,6 +421,10 @@ def main():
     from workload import make_config
 
     w = make_config(args.config)
+    if args.queries:
+        w["queries"] = w["queries"].subset(range(min(args.queries, len(w["queries"]))))
+    if args.db_limit:
+        w["db"] = w["db"].subset(range(min(args.db_limit, len(w["db"]))))
     if args.impl == "reference":
         run_reference(args, w)
     else:

@@ -87,6 +87,20 @@ int sw_db_free(sw_db *db);
 /* Sizes of a prepared database: sequence count, residue count, device bytes. */
 int sw_db_stats(const sw_db *db, int64_t *n_seqs, int64_t *residues, int64_t *device_bytes);
 
+/* Tuning knobs of a query batch; zero-initialise and set what you need.  Every
+ * field left at 0 takes its default.  (The paper's SW# splits database
+ * sequences between a short and a long kernel by length, Sec. 3.1.) */
+typedef struct sw_options {
+  int32_t cutover;         /* database units whose longer sequence has at least this many
+                              residues use the intra-task (multi-warp) kernel; 0 = 2048;
+                              a value above every length sends everything inter-task */
+  int32_t rows_per_lane;   /* query rows per lane of the inter-task kernel: 4, 8, 12, 16 or 24;
+                              0 = 16, or 8 for batches too small to fill the GPU */
+  int32_t lanes_per_chain; /* lanes per chain of the inter-task kernel, 4..32; 0 = chosen per query */
+  int32_t intra_rows;      /* query rows per lane of the intra-task kernel: 8 or 16; 0 = 16 */
+  int32_t reserved[4];     /* must be 0 */
+} sw_options;
+
 /*
  * sw_queries_prepare -- upload a batch of queries and plan the search.
  *
@@ -100,17 +114,15 @@ int sw_db_stats(const sw_db *db, int64_t *n_seqs, int64_t *residues, int64_t *de
  *   submat                          host pointer, 20x20 int8 (see above)
  *   gap_open, gap_extend            see the gap convention above
  *   mode                            SW_MODE_INT32 or SW_MODE_PACKED
- *   cutover                         database sequences at least this long use
- *                                   the intra-task (multi-warp) kernel; <= 0
- *                                   selects the built-in default (2048)
+ *   opts                            host pointer to tuning knobs, or NULL for defaults
  *   stream                          upload stream; the call returns after it completes
  *   out                             receives the new handle
  *
- * Errors: SW_EINVAL, SW_ENOMEM, SW_ECUDA.
+ * Errors: SW_EINVAL (bad arguments or knobs), SW_ENOMEM, SW_ECUDA.
  */
 int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q_offsets,
                        int64_t n_queries, const int8_t *submat, int32_t gap_open,
-                       int32_t gap_extend, int32_t mode, int32_t cutover, void *stream,
+                       int32_t gap_extend, int32_t mode, const sw_options *opts, void *stream,
                        sw_queries **out);
 
 /* Release a prepared query batch.  NULL is accepted. */
@@ -133,6 +145,19 @@ int sw_queries_free(sw_queries *q);
 int sw_search_prepared(const sw_db *db, const sw_queries *q, int32_t *scores_dev, void *stream);
 
 /*
+ * sw_search_graph -- the same search as sw_search_prepared, captured once into
+ * a CUDA graph and replayed.  The first call on q (and any later call with a
+ * different database or scores_dev) captures the whole enqueue sequence of
+ * sw_search_prepared on `stream` and instantiates it; every call then launches
+ * the graph on `stream`.  `stream` must not be the legacy default stream
+ * (NULL): stream capture needs a created stream.  Timing events
+ * (sw_queries_set_timing) are not recorded inside the graph.  The graph is
+ * released by sw_queries_free.  Errors: as sw_search_prepared, plus SW_EINVAL
+ * for a NULL stream.
+ */
+int sw_search_graph(const sw_db *db, sw_queries *q, int32_t *scores_dev, void *stream);
+
+/*
  * sw_queries_status -- read back the device status of the last search on q.
  * Synchronises `stream`.  *rescued receives the number of (query, sequence)
  * pairs whose packed score saturated and was recomputed in int32 (0 in int32
@@ -153,10 +178,12 @@ int sw_queries_kernel_ms(const sw_queries *q, void *stream, float *ms);
 
 /*
  * sw_queries_info -- sizes of a prepared batch: bytes copied host->device by
- * sw_queries_prepare (*h2d_bytes), device bytes it holds (*device_bytes) and
- * the number of DP tasks of the main kernel (*n_tasks).  Any output may be NULL.
+ * sw_queries_prepare (*h2d_bytes), device bytes it holds (*device_bytes), the
+ * number of DP tasks (*n_tasks) and the number of kernels one search launches
+ * (*launches).  Any output may be NULL.
  */
-int sw_queries_info(const sw_queries *q, int64_t *h2d_bytes, int64_t *device_bytes, int64_t *n_tasks);
+int sw_queries_info(const sw_queries *q, int64_t *h2d_bytes, int64_t *device_bytes, int64_t *n_tasks,
+                    int64_t *launches);
 
 /*
  * sw_search -- one-call search: prepare the queries, search, copy the scores

@@ -22,16 +22,24 @@ SIGNATURES = {
     "sw_db_prepare": (ctypes.c_int, [_p, _p, _i64, _p, _pp]),
     "sw_db_free": (ctypes.c_int, [_p]),
     "sw_db_stats": (ctypes.c_int, [_p, _pi64, _pi64, _pi64]),
-    "sw_queries_prepare": (ctypes.c_int, [_p, _p, _p, _i64, _p, _i32, _i32, _i32, _i32, _p, _pp]),
+    "sw_queries_prepare": (ctypes.c_int, [_p, _p, _p, _i64, _p, _i32, _i32, _i32, _p, _p, _pp]),
     "sw_queries_free": (ctypes.c_int, [_p]),
     "sw_search_prepared": (ctypes.c_int, [_p, _p, _p, _p]),
     "sw_queries_status": (ctypes.c_int, [_p, _p, _pi64]),
+    "sw_search_graph": (ctypes.c_int, [_p, _p, _p, _p]),
     "sw_search": (ctypes.c_int, [_p, _p, _p, _i64, _p, _i32, _i32, _i32, _p, _p]),
     "sw_queries_set_timing": (ctypes.c_int, [_p, _i32]),
     "sw_queries_kernel_ms": (ctypes.c_int, [_p, _p, ctypes.POINTER(ctypes.c_float)]),
-    "sw_queries_info": (ctypes.c_int, [_p, _pi64, _pi64, _pi64]),
+    "sw_queries_info": (ctypes.c_int, [_p, _pi64, _pi64, _pi64, _pi64]),
     "sw_last_error": (ctypes.c_char_p, []),
 }
+
+
+class SwOptions(ctypes.Structure):
+    """Mirror of sw_options (include/swgb.h); zero fields take defaults."""
+
+    _fields_ = [("cutover", ctypes.c_int32), ("rows_per_lane", ctypes.c_int32), ("lanes_per_chain", ctypes.c_int32),
+                ("intra_rows", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class SwError(RuntimeError):
@@ -87,10 +95,11 @@ def sw_db_stats(h):
     return a.value, b.value, c.value
 
 
-def sw_queries_prepare(db, q_ptr, qoff_ptr, n_queries, submat_ptr, gap_open, gap_extend, mode, cutover, stream):
+def sw_queries_prepare(db, q_ptr, qoff_ptr, n_queries, submat_ptr, gap_open, gap_extend, mode, opts, stream):
+    """opts: an SwOptions or None for defaults."""
     h = ctypes.c_void_p()
     check(lib().sw_queries_prepare(db, q_ptr, qoff_ptr, n_queries, submat_ptr, gap_open, gap_extend, mode,
-                                   cutover, stream, ctypes.byref(h)))
+                                   ctypes.byref(opts) if opts is not None else None, stream, ctypes.byref(h)))
     return h
 
 
@@ -124,6 +133,10 @@ def sw_queries_kernel_ms(qh, stream):
 
 
 def sw_queries_info(qh):
-    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
-    check(lib().sw_queries_info(qh, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
-    return a.value, b.value, c.value
+    a, b, c, d = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    check(lib().sw_queries_info(qh, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
+    return a.value, b.value, c.value, d.value
+
+
+def sw_search_graph(db, qh, scores_dev_ptr, stream):
+    return check(lib().sw_search_graph(db, qh, scores_dev_ptr, stream))

@@ -66,11 +66,16 @@ class Database:
             pass
 
 
+def options(cutover=0, rows_per_lane=0, lanes_per_chain=0, intra_rows=0):
+    """Tuning knobs of a query batch (sw_options); 0 keeps the default."""
+    return N.SwOptions(int(cutover), int(rows_per_lane), int(lanes_per_chain), int(intra_rows))
+
+
 class PreparedQueries:
     """A query batch uploaded and planned against one Database; search() is
     device-only and asynchronous (graph-capturable)."""
 
-    def __init__(self, db, residues, offsets, submat, gap_open=10, gap_extend=2, mode="packed", cutover=0,
+    def __init__(self, db, residues, offsets, submat, gap_open=10, gap_extend=2, mode="packed", opts=None,
                  stream=None):
         res, off = _seqs(residues, offsets)
         sm = np.ascontiguousarray(submat, dtype=np.int8)
@@ -79,7 +84,7 @@ class PreparedQueries:
         self.db = db
         self.nq = off.size - 1
         self.handle = N.sw_queries_prepare(db.handle, _ptr(res), _ptr(off), self.nq, _ptr(sm), int(gap_open),
-                                           int(gap_extend), _mode(mode), int(cutover), _stream(stream))
+                                           int(gap_extend), _mode(mode), opts, _stream(stream))
 
     def search(self, out=None, stream=None):
         import torch
@@ -91,6 +96,18 @@ class PreparedQueries:
         N.sw_search_prepared(self.db.handle, self.handle, ctypes.c_void_p(out.data_ptr()), _stream(stream))
         return out
 
+    def search_graph(self, out=None, stream=None):
+        """search() through a CUDA graph captured on the first call (needs a
+        non-default stream; pass a torch.cuda.Stream or run under one)."""
+        import torch
+
+        if out is None:
+            out = torch.empty((self.nq, self.db.n), dtype=torch.int32, device="cuda")
+        if not (out.is_cuda and out.dtype == torch.int32 and out.is_contiguous() and out.numel() == self.nq * self.db.n):
+            raise ValueError("out must be a contiguous int32 CUDA tensor of n_queries * n_db elements")
+        N.sw_search_graph(self.db.handle, self.handle, ctypes.c_void_p(out.data_ptr()), _stream(stream))
+        return out
+
     def set_timing(self, enable=True):
         N.sw_queries_set_timing(self.handle, enable)
 
@@ -99,7 +116,8 @@ class PreparedQueries:
         return N.sw_queries_kernel_ms(self.handle, _stream(stream))
 
     def info(self):
-        """(host->device bytes copied at prepare, device bytes held, DP tasks)."""
+        """(host->device bytes copied at prepare, device bytes held, DP tasks,
+        kernel launches per search)."""
         return N.sw_queries_info(self.handle)
 
     def status(self, stream=None):

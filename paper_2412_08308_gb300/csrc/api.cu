@@ -79,39 +79,51 @@ struct sw_db {
   size_t bytes = 0;
   int32_t max_npad = 0;
   double mean_npad = 0;
+  std::vector<int32_t> h_npad;  // padded lengths in sorted order
 };
 
 struct sw_queries {
   const sw_db *db = nullptr;
   int64_t nq = 0;
   int mode = SW_MODE_PACKED;
-  int R = 16;
+  int R = 16, Ri = 16;
   Scoring sc{};
-  std::vector<QDesc> qd;
-  int64_t n_units = 0;
-  int64_t n_tasks = 0, n_rtask_cap = 0;
-  int grid = 1, rgrid = 1;
-  int pbuf_bytes = 0;
-  size_t smem = 0;
-  int32_t gbuf_stride = 0;
+  std::vector<QDesc> qd, qdi;  // inter-task and intra-task plans per query
+  int64_t n_units = 0, n_long = 0;
+  int64_t n_tasks = 0, n_itasks = 0, n_itasks32 = 0, n_rtask_cap = 0;
+  bool inter_may_flag = false;  // some packed inter-task pair can exceed the 16-bit threshold
+  int grid = 1, rgrid = 1, igrid = 1, threads = 256;
+  int pbuf_bytes = 0, ipbuf_bytes = 0;
+  size_t smem = 0, ismem = 0;
+  int32_t gbuf_stride = 0, igbuf_stride = 0;
+  int64_t long_stride = 1;
   // device memory (one stream-ordered allocation)
   void *block = nullptr;
   size_t bytes = 0;
   cudaStream_t alloc_stream = nullptr;
+  cudaStream_t side = nullptr;  // second stream for the intra-task kernel
+  cudaEvent_t fork = nullptr, join = nullptr;
   uint8_t *d_qres = nullptr;
   int8_t *d_submat = nullptr;
-  QDesc *d_qd = nullptr;
-  Task *d_tasks = nullptr, *d_rtasks = nullptr;
-  int32_t *d_units = nullptr;
+  QDesc *d_qd = nullptr, *d_qdi = nullptr;
+  Task *d_tasks = nullptr, *d_itasks = nullptr, *d_itasks32 = nullptr, *d_rtasks = nullptr;
+  int32_t *d_units = nullptr, *d_ipos32 = nullptr;
   uint8_t *d_prof = nullptr;
   int64_t prof_bytes = 0;
-  uint2 *d_gbuf = nullptr;
-  int32_t *d_words = nullptr;  // [0] task counter, [1] rescue counter, [2] status, [3] rescue n_tasks, [4.. 4+nq) flag counts
-  int32_t *d_ntasks = nullptr; // constant: main n_tasks
-  int32_t *d_flag_pos = nullptr;
+  uint2 *d_gbuf = nullptr, *d_igbuf = nullptr;
+  int32_t *d_words = nullptr;
+  int32_t *d_flag_pos = nullptr, *d_iflag_pos = nullptr;
   int64_t h2d_bytes = 0;
   bool timing = false, timed = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaGraphExec_t gexec = nullptr;  // captured search (sw_search_graph)
+  const sw_db *gdb = nullptr;
+  int32_t *gscores = nullptr;
+  // word layout: [0] inter counter, [1] inter rescue counter, [2] status, [3] inter rescue tasks,
+  // [4] intra (packed) counter, [5] intra (int32) counter, [6], [7] unused,
+  // [8, 8+nq) inter flag counts, [8+nq, 8+2nq) intra flag counts   -- zeroed every search
+  // [8+2nq] inter tasks, [9+2nq] intra packed tasks, [10+2nq] intra int32 tasks -- constants
+  int64_t zero_words() const { return 8 + 2 * nq; }
 };
 
 namespace {
@@ -138,9 +150,19 @@ int choose_lanes(int m, int R, double mean_n) {
   return bestL;
 }
 
-int env_int(const char *name, int dflt) {
-  const char *v = getenv(name);
-  return v && *v ? atoi(v) : dflt;
+void free_queries(sw_queries *q) {
+  if (!q) return;
+  if (q->block) {
+    cudaFreeAsync(q->block, q->alloc_stream);
+    cudaStreamSynchronize(q->alloc_stream);
+  }
+  if (q->ev0) cudaEventDestroy(q->ev0);
+  if (q->ev1) cudaEventDestroy(q->ev1);
+  if (q->gexec) cudaGraphExecDestroy(q->gexec);
+  if (q->fork) cudaEventDestroy(q->fork);
+  if (q->join) cudaEventDestroy(q->join);
+  if (q->side) cudaStreamDestroy(q->side);
+  delete q;
 }
 
 }  // namespace
@@ -183,6 +205,7 @@ int sw_db_prepare(const uint8_t *residues, const int64_t *offsets, int64_t n_seq
     db->max_npad = std::max(db->max_npad, npad[k]);
   }
   db->mean_npad = n_seqs ? (double)padded / n_seqs : 0;
+  db->h_npad = npad;
   std::vector<uint8_t> packed((size_t)std::max<int64_t>(padded, 16), (uint8_t)kPadCode);
   for (int64_t k = 0; k < n_seqs; ++k)
     if (slen[k]) memcpy(&packed[off[k]], residues + offsets[order[k]], (size_t)slen[k]);
@@ -238,10 +261,9 @@ int sw_db_stats(const sw_db *db, int64_t *n_seqs, int64_t *residues, int64_t *de
 }
 
 int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int64_t n_queries,
-                       const int8_t *submat, int32_t gap_open, int32_t gap_extend, int32_t mode, int32_t cutover,
-                       void *stream, sw_queries **out) {
+                       const int8_t *submat, int32_t gap_open, int32_t gap_extend, int32_t mode,
+                       const sw_options *opts, void *stream, sw_queries **out) {
   g_err.clear();
-  (void)cutover;
   if (!out) return fail(SW_EINVAL, "sw_queries_prepare: null output handle");
   *out = nullptr;
   if (!db) return fail(SW_EINVAL, "sw_queries_prepare: null database");
@@ -249,6 +271,18 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   if (mode != SW_MODE_INT32 && mode != SW_MODE_PACKED) return fail(SW_EINVAL, "sw_queries_prepare: bad mode %d", mode);
   if (gap_open < 0 || gap_extend < 0 || (int64_t)gap_open + 2 * (int64_t)gap_extend > 1024)
     return fail(SW_EINVAL, "sw_queries_prepare: gap penalties out of range (%d, %d)", gap_open, gap_extend);
+  sw_options o{};
+  if (opts) o = *opts;
+  for (int i = 0; i < 4; ++i)
+    if (o.reserved[i]) return fail(SW_EINVAL, "sw_queries_prepare: reserved option fields must be 0");
+  int R = o.rows_per_lane ? o.rows_per_lane : 16;
+  const int Ri = o.intra_rows ? o.intra_rows : 16;
+  const int forceL = o.lanes_per_chain;
+  const int cutover = o.cutover > 0 ? o.cutover : 2048;
+  if (!inter_supported_R(R)) return fail(SW_EINVAL, "sw_queries_prepare: rows_per_lane must be 4, 8, 12, 16 or 24");
+  if (Ri != 8 && Ri != 16) return fail(SW_EINVAL, "sw_queries_prepare: intra_rows must be 8 or 16");
+  if (forceL && (forceL < 4 || forceL > 32)) return fail(SW_EINVAL, "sw_queries_prepare: lanes_per_chain must be 4..32");
+  if (o.cutover < 0) return fail(SW_EINVAL, "sw_queries_prepare: negative cutover");
   if (int rc = check_seqs(queries, q_offsets, n_queries, "sw_queries_prepare")) return rc;
   int smin = 127, smax = -128;
   for (int i = 0; i < kAlphabet * kAlphabet; ++i) {
@@ -267,48 +301,20 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   Q->nq = n_queries;
   Q->mode = mode;
   Q->alloc_stream = s;
+  Q->Ri = Ri;
   const bool packed = mode == SW_MODE_PACKED;
   Scoring &sc = Q->sc;
   sc.go = gap_open + gap_extend;
   sc.ge = gap_extend;
-  sc.kbias = std::max(0, -smin);
+  sc.pad = std::min(0, smin);
   sc.maxp = std::max(0, smax);
-  sc.bias = sc.go + sc.ge + sc.kbias;
   sc.thresh = 32767 - sc.maxp;
 
-  int R = env_int("SWGB_R", 16);
-  if (!inter_supported_R(R)) R = 16;
-  Q->R = R;
-  const int threads = inter_threads();
-  const int warps = threads / 32;
-  const double mean_n = std::max(16.0, db->mean_npad);
-  const int forceL = env_int("SWGB_L", 0);
-
-  // --- per-query plan
-  Q->qd.resize(n_queries);
-  int64_t prof = 0;
-  int maxc = 16;
-  bool chunked = false;
-  for (int64_t q = 0; q < n_queries; ++q) {
-    QDesc &d = Q->qd[q];
-    d.m = (int32_t)(q_offsets[q + 1] - q_offsets[q]);
-    d.R = R;
-    d.L = (forceL >= 4 && forceL <= 32) ? forceL : choose_lanes(std::max(1, d.m), R, mean_n);
-    const int LR = d.L * R;
-    d.nchunks = std::max(1, (d.m + LR - 1) / LR);
-    d.chunk_stride = (int32_t)round_up(LR, 128);
-    d.chunk_bytes = kProfRows * d.chunk_stride;
-    d.prof_off = prof;
-    d.qoff = q_offsets[q];
-    prof += (int64_t)d.nchunks * d.chunk_bytes;
-    maxc = std::max(maxc, d.chunk_bytes);
-    chunked |= d.nchunks > 1;
-  }
-  Q->prof_bytes = std::max<int64_t>(prof, 16);
-  Q->pbuf_bytes = (int)round_up(maxc, 128);
-
-  // --- units (sorted positions) and tasks, longest first
+  const int sms = sm_count(db->device);
   const int64_t n = db->n;
+  const std::vector<int32_t> &npad = db->h_npad;
+
+  // --- units (sorted positions); a unit is long when its first (longest) sequence reaches the cutover
   Q->n_units = packed ? (n + 1) / 2 : n;
   std::vector<int32_t> units(std::max<int64_t>(1, packed ? 2 * Q->n_units : n));
   if (packed) {
@@ -319,48 +325,169 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   } else {
     for (int64_t u = 0; u < n; ++u) units[u] = (int32_t)u;
   }
+  auto unit_len = [&](int64_t u) { return npad[units[packed ? 2 * u : u]]; };
+  int64_t n_long = 0;
+  while (n_long < Q->n_units && unit_len(n_long) >= cutover) ++n_long;
+  Q->n_long = n_long;
+  int32_t max_short = 16, max_long = 16;
+  double sum_short = 0;
+  for (int64_t u = n_long; u < Q->n_units; ++u) sum_short += unit_len(u);
+  if (n_long < Q->n_units) max_short = unit_len(n_long);
+  if (n_long) max_long = unit_len(0);
+  const double mean_n = Q->n_units > n_long ? std::max(16.0, sum_short / (Q->n_units - n_long)) : 16.0;
+
+  // --- rows per lane and CTA size of the inter-task kernel.  A small batch
+  // (few units x queries) cannot fill the GPU with 16-row lanes: halve the
+  // rows per lane (twice the lanes, half the per-step dependency chain), and
+  // shrink CTAs until the tasks cover every SM twice.
+  const int64_t n_short = Q->n_units - n_long;
+  auto lanes_needed = [&](int rr) {
+    double lanes = 0;
+    for (int64_t q = 0; q < n_queries; ++q) {
+      const int m = std::max<int>(1, (int)(q_offsets[q + 1] - q_offsets[q]));
+      lanes += (double)n_short * (forceL ? forceL : choose_lanes(m, rr, mean_n));
+    }
+    return lanes;
+  };
+  if (!o.rows_per_lane && lanes_needed(16) < (double)sms * 2048) R = 8;
+  Q->R = R;
+  int warps = inter_threads() / 32;
+  for (; warps > 2; warps /= 2) {
+    int64_t tasks = 0;
+    for (int64_t q = 0; q < n_queries; ++q) {
+      const int m = std::max<int>(1, (int)(q_offsets[q + 1] - q_offsets[q]));
+      const int chains = warps * (32 / (forceL ? forceL : choose_lanes(m, R, mean_n)));
+      tasks += (n_short + chains - 1) / chains;
+    }
+    if (tasks >= 2 * sms) break;
+  }
+  const int threads = warps * 32;
+  Q->threads = threads;
+
+  // --- per-query plans and profile layout
+  Q->qd.resize(n_queries);
+  Q->qdi.resize(n_queries);
+  int64_t prof = 0;
+  int maxc = 16, maxci = 16;
+  bool chunked = false, ichunked = false;
+  for (int64_t q = 0; q < n_queries; ++q) {
+    QDesc &d = Q->qd[q];
+    d.m = (int32_t)(q_offsets[q + 1] - q_offsets[q]);
+    d.R = R;
+    d.L = forceL ? forceL : choose_lanes(std::max(1, d.m), R, mean_n);
+    const int LR = d.L * R;
+    d.nchunks = std::max(1, (d.m + LR - 1) / LR);
+    d.chunk_stride = (int32_t)round_up(LR, 128);
+    d.chunk_bytes = kProfRows * d.chunk_stride;
+    d.prof_off = prof;
+    d.qoff = q_offsets[q];
+    prof += (int64_t)d.nchunks * d.chunk_bytes;
+    maxc = std::max(maxc, d.chunk_bytes);
+    chunked |= d.nchunks > 1;
+  }
+  if (n_long) {
+    const int wmax = intra_threads() / 32;
+    for (int64_t q = 0; q < n_queries; ++q) {
+      QDesc &d = Q->qdi[q];
+      d.m = Q->qd[q].m;
+      d.R = Ri;
+      const int w = (int)std::min<int64_t>(wmax, std::max<int64_t>(1, (d.m + 32 * Ri - 1) / (32 * Ri)));
+      d.L = 32 * w;
+      const int LR = d.L * Ri;
+      d.nchunks = std::max(1, (d.m + LR - 1) / LR);
+      d.chunk_stride = (int32_t)round_up(LR, 128);
+      d.chunk_bytes = kProfRows * d.chunk_stride;
+      d.prof_off = prof;
+      d.qoff = q_offsets[q];
+      prof += (int64_t)d.nchunks * d.chunk_bytes;
+      maxci = std::max(maxci, d.chunk_bytes);
+      ichunked |= d.nchunks > 1;
+    }
+  }
+  Q->prof_bytes = std::max<int64_t>(prof, 16);
+  Q->pbuf_bytes = (int)round_up(maxc, 128);
+  Q->ipbuf_bytes = (int)round_up(maxci, 128);
+
+  // --- tasks, longest first
   struct TW {
     Task t;
     double w;
   };
-  std::vector<TW> tw;
-  std::vector<int32_t> h_npad;
-  if (n) {
-    h_npad.resize(n);
-    SW_CUDA(cudaMemcpy(h_npad.data(), db->view.npad, 4 * n, cudaMemcpyDeviceToHost), "sw_queries_prepare: read db");
-  }
+  std::vector<TW> tw, twi, twi32;
+  std::vector<int32_t> ipos32;  // database positions of the int32 intra-task units
   int64_t rcap = 0;
-  for (int64_t q = 0; q < n_queries && Q->n_units > 0; ++q) {
+  // a pair scores at most max(SM) * min(m, n): a packed lane that cannot pass the
+  // threshold needs no rescue pass
+  auto may_flag = [&](int64_t q, int32_t n_upper) {
+    return packed && (int64_t)sc.maxp * std::min<int64_t>(Q->qd[q].m, n_upper) > sc.thresh;
+  };
+  for (int64_t q = 0; q < n_queries && Q->n_units > n_long; ++q) {
     const QDesc &d = Q->qd[q];
     const int chains = warps * (32 / d.L);
-    for (int64_t u0 = 0; u0 < Q->n_units; u0 += chains) {
-      Task t;
-      t.q = (int32_t)q;
-      t.unit_begin = (int32_t)u0;
-      t.unit_count = (int32_t)std::min<int64_t>(chains, Q->n_units - u0);
-      t.pad_ = 0;
-      const int32_t first = units[packed ? 2 * u0 : u0];
-      tw.push_back({t, (double)d.nchunks * d.L * d.R * (h_npad[first] + d.L + 8)});
+    for (int64_t u0 = n_long; u0 < Q->n_units; u0 += chains) {
+      Task t{(int32_t)q, (int32_t)u0, (int32_t)std::min<int64_t>(chains, Q->n_units - u0), 0};
+      tw.push_back({t, (double)d.nchunks * d.L * d.R * (unit_len(u0) + d.L + 8)});
     }
     rcap += (n + chains - 1) / chains;
+    Q->inter_may_flag |= may_flag(q, max_short);
+  }
+  // long units: packed intra-task kernel where no lane can saturate, int32
+  // otherwise (recomputing a saturated long matrix would cost more than
+  // computing it once in int32)
+  for (int64_t q = 0; q < n_queries && n_long; ++q) {
+    const QDesc &d = Q->qdi[q];
+    for (int64_t u = 0; u < n_long; ++u) {
+      const double w = (double)d.nchunks * d.L * d.R * (unit_len(u) + d.L);
+      if (packed && !may_flag(q, unit_len(u))) {
+        twi.push_back({Task{(int32_t)q, (int32_t)u, 1, 0}, w});
+        continue;
+      }
+      const int32_t a = units[packed ? 2 * u : u];
+      const int32_t b = packed ? units[2 * u + 1] : a;
+      twi32.push_back({Task{(int32_t)q, (int32_t)ipos32.size(), 1, 0}, 2 * w});
+      ipos32.push_back(a);
+      if (b != a) {
+        twi32.push_back({Task{(int32_t)q, (int32_t)ipos32.size(), 1, 0}, 2 * w});
+        ipos32.push_back(b);
+      }
+    }
   }
   std::stable_sort(tw.begin(), tw.end(), [](const TW &a, const TW &b) { return a.w > b.w; });
+  std::stable_sort(twi.begin(), twi.end(), [](const TW &a, const TW &b) { return a.w > b.w; });
+  std::stable_sort(twi32.begin(), twi32.end(), [](const TW &a, const TW &b) { return a.w > b.w; });
   Q->n_tasks = (int64_t)tw.size();
-  Q->n_rtask_cap = packed ? rcap : 0;
+  Q->n_itasks = (int64_t)twi.size();
+  Q->n_itasks32 = (int64_t)twi32.size();
+  Q->long_stride = std::max<int64_t>(1, packed ? 2 * n_long : n_long);
+  Q->n_rtask_cap = Q->inter_may_flag ? rcap : 0;
 
   // --- launch geometry
-  const int sms = sm_count(db->device);
   Q->smem = inter_smem_bytes(Q->pbuf_bytes, threads);
-  if (Q->smem > 200 * 1024) {
+  Q->ismem = intra_smem_bytes(Q->ipbuf_bytes);
+  if (Q->smem > 200 * 1024 || (n_long && Q->ismem > 220 * 1024)) {
     delete Q;
-    return fail(SW_EINVAL, "sw_queries_prepare: profile chunk too large");
+    return fail(SW_EINVAL, "sw_queries_prepare: profile chunk too large for shared memory");
   }
   const int occ = inter_max_ctas_per_sm(R, packed, threads, Q->smem);
   const int occ32 = inter_max_ctas_per_sm(R, false, threads, Q->smem);
+  if (occ <= 0 || occ32 <= 0) {
+    delete Q;
+    return fail(SW_ECUDA, "sw_queries_prepare: cannot configure the inter-task kernel");
+  }
+  if (n_long) {
+    cudaError_t ce = configure_intra(Ri, packed);
+    if (ce == cudaSuccess && packed) ce = configure_intra(Ri, false);
+    if (ce != cudaSuccess) {
+      delete Q;
+      return cuda_fail(ce, "sw_queries_prepare: cannot configure the intra-task kernel");
+    }
+  }
   Q->grid = (int)std::max<int64_t>(1, std::min<int64_t>(Q->n_tasks, (int64_t)sms * occ));
   Q->rgrid = std::max(1, sms * occ32);
+  Q->igrid = (int)std::max<int64_t>(1, std::min<int64_t>(std::max(Q->n_itasks, Q->n_itasks32), sms));
   const int gslots = std::max(Q->grid, Q->rgrid);
-  Q->gbuf_stride = chunked ? (int32_t)round_up(std::max(16, db->max_npad), 16) : 2;
+  Q->gbuf_stride = chunked ? (int32_t)round_up(std::max<int32_t>(16, max_short), 16) : 2;
+  Q->igbuf_stride = ichunked ? (int32_t)round_up(std::max<int32_t>(16, max_long), 16) : 2;
 
   // --- device allocation (stream ordered)
   const int64_t nqm = std::max<int64_t>(n_queries, 1);
@@ -368,13 +495,19 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   const size_t b_sub = 512;
   const size_t b_qd = round_up(sizeof(QDesc) * nqm, 256);
   const size_t b_tasks = round_up(sizeof(Task) * std::max<int64_t>(Q->n_tasks, 1), 256);
+  const size_t b_itasks = round_up(sizeof(Task) * std::max<int64_t>(Q->n_itasks, 1), 256);
+  const size_t b_itasks32 = round_up(sizeof(Task) * std::max<int64_t>(Q->n_itasks32, 1), 256);
+  const size_t b_ipos32 = round_up(4 * std::max<int64_t>((int64_t)ipos32.size(), 1), 256);
   const size_t b_rtasks = round_up(sizeof(Task) * std::max<int64_t>(Q->n_rtask_cap, 1), 256);
   const size_t b_units = round_up(4 * (int64_t)units.size(), 256);
   const size_t b_prof = round_up(Q->prof_bytes, 256);
   const size_t b_gbuf = round_up((int64_t)gslots * warps * 8 * (int64_t)Q->gbuf_stride * 8, 256);
-  const size_t b_words = round_up(4 * (8 + nqm), 256);
-  const size_t b_flag = packed ? round_up(4 * nqm * std::max<int64_t>(n, 1), 256) : 0;
-  Q->bytes = b_qres + b_sub + b_qd + b_tasks + b_rtasks + b_units + b_prof + b_gbuf + b_words + b_flag;
+  const size_t b_igbuf = round_up((int64_t)Q->igrid * (int64_t)Q->igbuf_stride * 8, 256);
+  const size_t b_words = round_up(4 * (12 + 2 * nqm), 256);  // zeroed words + 3 constants
+  const size_t b_flag = Q->inter_may_flag ? round_up(4 * nqm * std::max<int64_t>(n, 1), 256) : 0;
+  const size_t b_iflag = packed ? round_up(4 * nqm * Q->long_stride, 256) : 0;
+  Q->bytes = b_qres + b_sub + 2 * b_qd + b_tasks + b_itasks + b_itasks32 + b_ipos32 + b_rtasks + b_units + b_prof +
+             b_gbuf + b_igbuf + b_words + b_flag + b_iflag;
   cudaError_t e = cudaMallocAsync(&Q->block, Q->bytes, s);
   if (e != cudaSuccess) {
     delete Q;
@@ -389,35 +522,57 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   Q->d_qres = take(b_qres);
   Q->d_submat = (int8_t *)take(b_sub);
   Q->d_qd = (QDesc *)take(b_qd);
+  Q->d_qdi = (QDesc *)take(b_qd);
   Q->d_tasks = (Task *)take(b_tasks);
+  Q->d_itasks = (Task *)take(b_itasks);
+  Q->d_itasks32 = (Task *)take(b_itasks32);
+  Q->d_ipos32 = (int32_t *)take(b_ipos32);
   Q->d_rtasks = (Task *)take(b_rtasks);
   Q->d_units = (int32_t *)take(b_units);
   Q->d_prof = take(b_prof);
   Q->d_gbuf = (uint2 *)take(b_gbuf);
+  Q->d_igbuf = (uint2 *)take(b_igbuf);
   Q->d_words = (int32_t *)take(b_words);
-  Q->d_flag_pos = packed ? (int32_t *)take(b_flag) : nullptr;
-  Q->d_ntasks = Q->d_words + 4 + nqm + 1;  // past the zeroed region
+  Q->d_flag_pos = Q->inter_may_flag ? (int32_t *)take(b_flag) : nullptr;
+  Q->d_iflag_pos = packed ? (int32_t *)take(b_iflag) : nullptr;
 
-  Q->h2d_bytes = q_offsets[n_queries] + 400 + (int64_t)sizeof(QDesc) * n_queries + (int64_t)sizeof(Task) * Q->n_tasks +
-                 4 * (int64_t)units.size() + 4;
-  std::vector<Task> tasks(Q->n_tasks);
+  std::vector<Task> tasks(Q->n_tasks), itasks(Q->n_itasks), itasks32(Q->n_itasks32);
   for (int64_t i = 0; i < Q->n_tasks; ++i) tasks[i] = tw[i].t;
-  int32_t nt32 = (int32_t)Q->n_tasks;
+  for (int64_t i = 0; i < Q->n_itasks; ++i) itasks[i] = twi[i].t;
+  for (int64_t i = 0; i < Q->n_itasks32; ++i) itasks32[i] = twi32[i].t;
+  const int32_t consts[3] = {(int32_t)Q->n_tasks, (int32_t)Q->n_itasks, (int32_t)Q->n_itasks32};
+  Q->h2d_bytes = q_offsets[n_queries] + 400 + 2 * (int64_t)sizeof(QDesc) * n_queries +
+                 (int64_t)sizeof(Task) * (Q->n_tasks + Q->n_itasks + Q->n_itasks32) + 4 * (int64_t)units.size() +
+                 4 * (int64_t)ipos32.size() + 12;
   e = cudaSuccess;
   if (q_offsets[n_queries] > 0)
     e = cudaMemcpyAsync(Q->d_qres, queries, q_offsets[n_queries], cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(Q->d_submat, submat, 400, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && n_queries)
     e = cudaMemcpyAsync(Q->d_qd, Q->qd.data(), sizeof(QDesc) * n_queries, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && n_queries && n_long)
+    e = cudaMemcpyAsync(Q->d_qdi, Q->qdi.data(), sizeof(QDesc) * n_queries, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && Q->n_tasks)
     e = cudaMemcpyAsync(Q->d_tasks, tasks.data(), sizeof(Task) * Q->n_tasks, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && Q->n_itasks)
+    e = cudaMemcpyAsync(Q->d_itasks, itasks.data(), sizeof(Task) * Q->n_itasks, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && Q->n_itasks32) {
+    e = cudaMemcpyAsync(Q->d_itasks32, itasks32.data(), sizeof(Task) * Q->n_itasks32, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(Q->d_ipos32, ipos32.data(), 4 * ipos32.size(), cudaMemcpyHostToDevice, s);
+  }
   if (e == cudaSuccess) e = cudaMemcpyAsync(Q->d_units, units.data(), 4 * units.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(Q->d_words, 0, b_words, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(Q->d_ntasks, &nt32, 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(Q->d_words + Q->zero_words(), consts, sizeof consts, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && n_long) {
+    e = cudaStreamCreateWithFlags(&Q->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&Q->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&Q->join, cudaEventDisableTiming);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
-    cudaFreeAsync(Q->block, s);
-    delete Q;
+    free_queries(Q);
     return cuda_fail(e, "sw_queries_prepare: upload");
   }
   *out = Q;
@@ -426,14 +581,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
 
 int sw_queries_free(sw_queries *q) {
   g_err.clear();
-  if (!q) return SW_OK;
-  if (q->block) {
-    cudaFreeAsync(q->block, q->alloc_stream);
-    cudaStreamSynchronize(q->alloc_stream);
-  }
-  if (q->ev0) cudaEventDestroy(q->ev0);
-  if (q->ev1) cudaEventDestroy(q->ev1);
-  delete q;
+  free_queries(q);
   return SW_OK;
 }
 
@@ -445,49 +593,120 @@ int sw_search_prepared(const sw_db *db, const sw_queries *Q, int32_t *scores_dev
   if (!scores_dev) return fail(SW_EINVAL, "sw_search_prepared: null scores");
   cudaStream_t s = (cudaStream_t)stream;
   const bool packed = Q->mode == SW_MODE_PACKED;
-  const int threads = inter_threads();
+  const int threads = Q->threads;
+  const int nq = (int)Q->nq;
+  int32_t *w = Q->d_words;
 
-  SW_CUDA(cudaMemsetAsync(Q->d_words, 0, 4 * (4 + Q->nq), s), "memset");
-  SW_CUDA(launch_build_profiles(Q->d_qres, Q->d_qd, (int32_t)Q->nq, Q->d_submat, Q->sc.kbias, Q->d_prof, s),
-          "profile kernel");
+  SW_CUDA(cudaMemsetAsync(w, 0, 4 * Q->zero_words(), s), "memset");
+  SW_CUDA(launch_build_profiles(Q->d_qres, Q->d_qd, nq, Q->d_submat, Q->sc.pad, Q->d_prof, s), "profile kernel");
+  if (Q->n_long)
+    SW_CUDA(launch_build_profiles(Q->d_qres, Q->d_qdi, nq, Q->d_submat, Q->sc.pad, Q->d_prof, s),
+            "profile kernel");
 
   InterArgs a{};
   a.db = db->view;
   a.unit_pos = Q->d_units;
-  a.qd = Q->d_qd;
-  a.tasks = Q->d_tasks;
-  a.n_tasks = Q->d_ntasks;
-  a.task_counter = Q->d_words + 0;
   a.prof = Q->d_prof;
-  a.pbuf_bytes = Q->pbuf_bytes;
-  a.gbuf = Q->d_gbuf;
-  a.gbuf_stride = Q->gbuf_stride;
   a.out = scores_dev;
   a.out_stride = db->n;
-  a.flag_count = Q->d_words + 4;
-  a.flag_pos = Q->d_flag_pos;
   a.sc = Q->sc;
-  a.status = Q->d_words + 2;
-  if (Q->timing) SW_CUDA(cudaEventRecord(Q->ev0, s), "event");
-  SW_CUDA(launch_inter(a, Q->R, packed, Q->grid, threads, Q->smem, s), "DP kernel");
-  if (Q->timing) {
-    SW_CUDA(cudaEventRecord(Q->ev1, s), "event");
-    const_cast<sw_queries *>(Q)->timed = true;
+  a.status = w + 2;
+
+  // long database units: intra-task kernel on the side stream, concurrently
+  if (Q->n_long) {
+    SW_CUDA(cudaEventRecord(Q->fork, s), "event");
+    SW_CUDA(cudaStreamWaitEvent(Q->side, Q->fork, 0), "event");
+    InterArgs b = a;
+    b.qd = Q->d_qdi;
+    b.pbuf_bytes = Q->ipbuf_bytes;
+    b.gbuf = Q->d_igbuf;
+    b.gbuf_stride = Q->igbuf_stride;
+    b.flag_count = w + 8 + nq;
+    b.flag_pos = Q->d_iflag_pos;
+    b.flag_stride = Q->long_stride;
+    if (Q->n_itasks) {  // packed units that cannot saturate
+      b.tasks = Q->d_itasks;
+      b.n_tasks = w + Q->zero_words() + 1;
+      b.task_counter = w + 4;
+      SW_CUDA(launch_intra(b, Q->Ri, true, Q->igrid, Q->ismem, Q->side), "intra-task kernel");
+    }
+    if (Q->n_itasks32) {  // single sequences in int32
+      b.unit_pos = Q->d_ipos32;
+      b.tasks = Q->d_itasks32;
+      b.n_tasks = w + Q->zero_words() + 2;
+      b.task_counter = w + 5;
+      SW_CUDA(launch_intra(b, Q->Ri, false, Q->igrid, Q->ismem, Q->side), "intra-task kernel (int32)");
+    }
+    SW_CUDA(cudaEventRecord(Q->join, Q->side), "event");
   }
 
-  if (packed) {
-    SW_CUDA(launch_rescue_tasks(Q->d_words + 4, Q->d_qd, (int32_t)Q->nq, db->n, threads / 32, Q->d_rtasks,
-                                Q->d_words + 3, Q->d_words + 1, s),
-            "rescue task kernel");
-    InterArgs r = a;
-    r.unit_pos = Q->d_flag_pos;
-    r.tasks = Q->d_rtasks;
-    r.n_tasks = Q->d_words + 3;
-    r.task_counter = Q->d_words + 1;
-    r.flag_count = nullptr;
-    r.flag_pos = nullptr;
-    SW_CUDA(launch_inter(r, Q->R, false, Q->rgrid, threads, Q->smem, s), "rescue kernel");
+  if (Q->n_tasks) {
+    a.qd = Q->d_qd;
+    a.tasks = Q->d_tasks;
+    a.n_tasks = w + Q->zero_words();
+    a.task_counter = w + 0;
+    a.pbuf_bytes = Q->pbuf_bytes;
+    a.gbuf = Q->d_gbuf;
+    a.gbuf_stride = Q->gbuf_stride;
+    a.flag_count = w + 8;
+    a.flag_pos = Q->d_flag_pos;
+    a.flag_stride = db->n;
+    if (Q->timing) SW_CUDA(cudaEventRecord(Q->ev0, s), "event");
+    SW_CUDA(launch_inter(a, Q->R, packed, Q->grid, threads, Q->smem, s), "inter-task kernel");
+    if (Q->timing) {
+      SW_CUDA(cudaEventRecord(Q->ev1, s), "event");
+      const_cast<sw_queries *>(Q)->timed = true;
+    }
+    if (Q->inter_may_flag) {
+      SW_CUDA(launch_rescue_tasks(w + 8, Q->d_qd, nq, db->n, threads / 32, 0, Q->d_rtasks, w + 3, w + 1, s),
+              "rescue task kernel");
+      InterArgs r = a;
+      r.unit_pos = Q->d_flag_pos;
+      r.tasks = Q->d_rtasks;
+      r.n_tasks = w + 3;
+      r.task_counter = w + 1;
+      r.flag_count = nullptr;
+      r.flag_pos = nullptr;
+      SW_CUDA(launch_inter(r, Q->R, false, Q->rgrid, threads, Q->smem, s), "inter-task rescue kernel");
+    }
   }
+  if (Q->n_long) SW_CUDA(cudaStreamWaitEvent(s, Q->join, 0), "event");
+  return SW_OK;
+}
+
+int sw_search_graph(const sw_db *db, sw_queries *Q, int32_t *scores_dev, void *stream) {
+  g_err.clear();
+  if (!db || !Q) return fail(SW_EINVAL, "sw_search_graph: null handle");
+  if (!stream) return fail(SW_EINVAL, "sw_search_graph: stream capture needs a non-default stream");
+  if (Q->nq == 0 || db->n == 0) return SW_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!Q->gexec || Q->gdb != db || Q->gscores != scores_dev) {
+    if (Q->gexec) {
+      cudaGraphExecDestroy(Q->gexec);
+      Q->gexec = nullptr;
+    }
+    SW_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+    const bool timing = Q->timing;
+    Q->timing = false;
+    int rc = sw_search_prepared(db, Q, scores_dev, stream);
+    Q->timing = timing;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &graph);
+    if (rc != SW_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&Q->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      Q->gexec = nullptr;
+      return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    Q->gdb = db;
+    Q->gscores = scores_dev;
+  }
+  SW_CUDA(cudaGraphLaunch(Q->gexec, s), "cudaGraphLaunch");
   return SW_OK;
 }
 
@@ -495,16 +714,17 @@ int sw_queries_status(const sw_queries *Q, void *stream, int64_t *rescued) {
   g_err.clear();
   if (!Q) return fail(SW_EINVAL, "sw_queries_status: null handle");
   cudaStream_t s = (cudaStream_t)stream;
-  std::vector<int32_t> w(4 + Q->nq);
+  std::vector<int32_t> w(Q->zero_words());
   SW_CUDA(cudaMemcpyAsync(w.data(), Q->d_words, 4 * w.size(), cudaMemcpyDeviceToHost, s), "status read");
   SW_CUDA(cudaStreamSynchronize(s), "status sync");
-  if (rescued) {
-    int64_t t = 0;
-    if (Q->mode == SW_MODE_PACKED)
-      for (int64_t q = 0; q < Q->nq; ++q) t += w[4 + q];
-    *rescued = t;
+  int64_t inter_flags = 0, intra_flags = 0;
+  for (int64_t q = 0; q < Q->nq; ++q) {
+    inter_flags += w[8 + q];
+    intra_flags += w[8 + Q->nq + q];
   }
+  if (rescued) *rescued = inter_flags;
   if (w[2] == SW_ETIMEOUT) return fail(SW_ETIMEOUT, "a bounded device wait expired");
+  if (intra_flags) return fail(SW_ECUDA, "internal error: a packed intra-task lane passed its bound");
   return SW_OK;
 }
 
@@ -529,12 +749,23 @@ int sw_queries_kernel_ms(const sw_queries *q, void *stream, float *ms) {
   return SW_OK;
 }
 
-int sw_queries_info(const sw_queries *q, int64_t *h2d_bytes, int64_t *device_bytes, int64_t *n_tasks) {
+int sw_queries_info(const sw_queries *q, int64_t *h2d_bytes, int64_t *device_bytes, int64_t *n_tasks,
+                    int64_t *launches) {
   g_err.clear();
   if (!q) return fail(SW_EINVAL, "sw_queries_info: null handle");
+  if (launches) {
+    int64_t k = 0;
+    if (q->nq > 0 && q->db->n > 0) {
+      k = 1 + (q->n_long ? 1 : 0);                       // profile builds
+      k += q->n_tasks ? 1 : 0;                            // inter-task kernel
+      k += (q->n_tasks && q->inter_may_flag) ? 2 : 0;     // rescue tasks + int32 rescue
+      k += (q->n_itasks ? 1 : 0) + (q->n_itasks32 ? 1 : 0);
+    }
+    *launches = k;
+  }
   if (h2d_bytes) *h2d_bytes = q->h2d_bytes;
   if (device_bytes) *device_bytes = (int64_t)q->bytes;
-  if (n_tasks) *n_tasks = q->n_tasks;
+  if (n_tasks) *n_tasks = q->n_tasks + q->n_itasks + q->n_itasks32;
   return SW_OK;
 }
 
@@ -545,7 +776,8 @@ int sw_search(const sw_db *db, const uint8_t *queries, const int64_t *q_offsets,
   if (!db) return fail(SW_EINVAL, "sw_search: null database");
   if (n_queries > 0 && db->n > 0 && !scores_out) return fail(SW_EINVAL, "sw_search: null scores");
   sw_queries *Q = nullptr;
-  int rc = sw_queries_prepare(db, queries, q_offsets, n_queries, submat, gap_open, gap_extend, mode, 0, stream, &Q);
+  int rc = sw_queries_prepare(db, queries, q_offsets, n_queries, submat, gap_open, gap_extend, mode, nullptr, stream,
+                              &Q);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t count = n_queries * db->n;
@@ -555,7 +787,7 @@ int sw_search(const sw_db *db, const uint8_t *queries, const int64_t *q_offsets,
   if (count > 0 && !dev) {
     cudaError_t e = cudaMallocAsync(&tmp, 4 * count, s);
     if (e != cudaSuccess) {
-      sw_queries_free(Q);
+      free_queries(Q);
       return cuda_fail(e, "sw_search: score buffer");
     }
     dst = (int32_t *)tmp;
@@ -568,7 +800,7 @@ int sw_search(const sw_db *db, const uint8_t *queries, const int64_t *q_offsets,
   if (rc == SW_OK) rc = sw_queries_status(Q, stream, nullptr);
   if (tmp) cudaFreeAsync(tmp, s);
   std::string keep = g_err;
-  sw_queries_free(Q);
+  free_queries(Q);
   g_err = keep;
   return rc;
 }

@@ -2,11 +2,14 @@
 // step of R query rows owned by one lane (Sec. 2.2 Eqs. 1-3).
 //
 // int32 form: Algorithm 1's statements, one cell per lane op.
-// packed form: two cells per 32-bit word.  Each 16-bit half holds the true
-// value plus a bias B >= Go + Ge + K, so every intermediate of a cell update
-// lies in [0, 32767] as long as the pair's score stays below 32767 - max(SM):
-// additions are plain 32-bit IADD/IADD3 (no carry or borrow crosses the
-// halves) and maxima are per-half VIMNMX (__vmaxs2), all full-rate on sm_103.
+// packed form: two cells per 32-bit word, each 16-bit half a signed cell value.
+// On sm_103 the integer ALU pipe (which executes every max, PRMT and IADD)
+// issues a warp instruction every second cycle, and the FMA pipe is a second
+// pipe of the same width that executes the per-half 16x2 adds (__vadd2 /
+// __vsub2).  So a word update spends its 5 maxima on the ALU pipe (the zero
+// floor of Eq. 1 is free in __vimax_s16x2_relu) and its 4 additions on the FMA
+// pipe.  Per-half adds never carry into the other half; a half whose running
+// score exceeds 32767 - max(SM) may have wrapped and is recomputed in int32.
 #pragma once
 
 #include <cstdint>
@@ -19,24 +22,21 @@ namespace swgb {
 constexpr uint32_t kPadPair = 20u | (20u << 16);
 
 struct Consts {
-  // packed
-  uint32_t goW, geW, bW, negKW, H0W, F0W, E0W;
+  // packed: (x, x) in both 16-bit halves
+  uint32_t goW, geW, F0W, E0W;
   // int32
-  int32_t go, ge, k;
+  int32_t go, ge;
 };
 
 __device__ __forceinline__ Consts make_consts(const Scoring &sc) {
   Consts c;
   c.goW = (uint32_t)sc.go * 0x10001u;
   c.geW = (uint32_t)sc.ge * 0x10001u;
-  c.bW = (uint32_t)sc.bias * 0x10001u;
-  c.negKW = 0u - (uint32_t)sc.kbias * 0x10001u;
-  c.H0W = c.bW;
-  c.F0W = (uint32_t)(sc.bias - sc.go) * 0x10001u;
+  const uint32_t ngo = (uint32_t)(-sc.go) & 0xffffu;  // E, F start at -Go (any value <= 0 works)
+  c.F0W = ngo | (ngo << 16);
   c.E0W = c.F0W;
   c.go = sc.go;
   c.ge = sc.ge;
-  c.k = sc.kbias;
   return c;
 }
 
@@ -50,10 +50,15 @@ __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
   return d;
 }
 
-// Selectors: pair(i) -> (byte i of a, 0, byte i of b, 0) for bytes < 128 (the
-// sign of such a byte is 0); one(i) -> byte i of a, zero-extended from b = 0.
+// Selectors.  pair(i) -> (byte i of a, its sign, byte i of b, its sign): the two
+// bytes sign-extended into the 16-bit halves (residue codes < 128 come out
+// zero-extended).  sext(i) -> byte i of a sign-extended to 32 bits.
+// one(i) -> byte i of a, zero-extended from b = 0.
 __host__ __device__ constexpr uint32_t sel_pair(int i) {
   return (uint32_t)i | ((uint32_t)(i | 8) << 4) | ((uint32_t)(4 + i) << 8) | ((uint32_t)((4 + i) | 8) << 12);
+}
+__host__ __device__ constexpr uint32_t sel_sext(int i) {
+  return (uint32_t)i | ((uint32_t)(i | 8) << 4) | ((uint32_t)(i | 8) << 8) | ((uint32_t)(i | 8) << 12);
 }
 __host__ __device__ constexpr uint32_t sel_one(int i) { return 0x4440u | (uint32_t)i; }
 
@@ -96,14 +101,13 @@ struct LaneState {
 template <int R, bool PACKED>
 __device__ __forceinline__ void lane_reset(LaneState<R, PACKED> &st, const Consts &cs) {
   using W = Word<PACKED>;
-  const W H0 = PACKED ? (W)cs.H0W : (W)0;
   const W E0 = PACKED ? (W)cs.E0W : (W)0;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    st.Hl[r] = H0;
+    st.Hl[r] = (W)0;
     st.E[r] = E0;
   }
-  st.hdiag = H0;
+  st.hdiag = (W)0;
 }
 
 // One column: inputs are the (H, F) pair passed down from the row above this
@@ -124,15 +128,14 @@ __device__ __forceinline__ void column_step(LaneState<R, PACKED> &st, const uint
     uint32_t hd = (uint32_t)st.hdiag, f = (uint32_t)inF;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const uint32_t p = prmt(pa[r >> 2], pb[r >> 2], sel_pair(r & 3));
-      const uint32_t x = hd + p + cs.negKW;
-      uint32_t tt = __vmaxs2(x, (uint32_t)st.E[r]);
-      tt = __vmaxs2(tt, cs.bW);
+      const uint32_t p = prmt(pa[r >> 2], pb[r >> 2], sel_pair(r & 3));  // (SM_a, SM_b), signed halves
+      const uint32_t x = __vadd2(hd, p);                                  // FMA pipe
+      const uint32_t tt = __vimax_s16x2_relu(x, (uint32_t)st.E[r]);      // max(x, E, 0)
       const uint32_t h = __vmaxs2(tt, f);
       S = (W)__vmaxs2((uint32_t)S, h);
-      const uint32_t hgo = h - cs.goW;
-      st.E[r] = (W)__vmaxs2((uint32_t)st.E[r] - cs.geW, hgo);
-      f = __vmaxs2(f - cs.geW, hgo);
+      const uint32_t hgo = __vsub2(h, cs.goW);
+      st.E[r] = (W)__vmaxs2(__vsub2((uint32_t)st.E[r], cs.geW), hgo);
+      f = __vmaxs2(__vsub2(f, cs.geW), hgo);
       hd = (uint32_t)st.Hl[r];
       st.Hl[r] = (W)h;
     }
@@ -143,7 +146,7 @@ __device__ __forceinline__ void column_step(LaneState<R, PACKED> &st, const uint
     int32_t hul = (int32_t)st.hdiag, hu = (int32_t)inH, fu = (int32_t)inF;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const int32_t sm = (int32_t)prmt(pa[r >> 2], 0u, sel_one(r & 3)) - cs.k;
+      const int32_t sm = (int32_t)prmt(pa[r >> 2], 0u, sel_sext(r & 3));
       const int32_t e1 = (int32_t)st.E[r] - cs.ge;
       const int32_t e2 = (int32_t)st.Hl[r] - cs.go;
       const int32_t e = max(e1, e2);
@@ -176,23 +179,27 @@ __device__ __forceinline__ Word<PACKED> score_max(Word<PACKED> a, Word<PACKED> b
 // Epilogue for one database unit: un-bias, flag possible overflows (packed)
 // and scatter to caller order.
 template <bool PACKED>
-__device__ __forceinline__ void write_scores(Word<PACKED> S, int posA, int posB, int q, const DbView &db,
-                                             const Scoring &sc, int32_t *out, int64_t out_stride,
-                                             int32_t *flag_count, int32_t *flag_pos) {
-  const int64_t row = (int64_t)q * out_stride;
+__device__ __forceinline__ void write_scores(Word<PACKED> S, int posA, int posB, int q, const InterArgs &a) {
+  const DbView &db = a.db;
+  const Scoring &sc = a.sc;
+  int32_t *out = a.out;
+  int32_t *flag_count = a.flag_count;
+  int32_t *flag_pos = a.flag_pos;
+  const int64_t row = (int64_t)q * a.out_stride;
+  const int64_t frow = (int64_t)q * a.flag_stride;
   if constexpr (PACKED) {
     const int32_t sa = (int32_t)((uint32_t)S & 0xffffu), sb = (int32_t)((uint32_t)S >> 16);
     if (sa > sc.thresh) {
       const int i = atomicAdd(&flag_count[q], 1);
-      flag_pos[row + i] = posA;
+      flag_pos[frow + i] = posA;
     }
-    out[row + db.perm[posA]] = sa - sc.bias;
+    out[row + db.perm[posA]] = sa;
     if (posB != posA) {
       if (sb > sc.thresh) {
         const int i = atomicAdd(&flag_count[q], 1);
-        flag_pos[row + i] = posB;
+        flag_pos[frow + i] = posB;
       }
-      out[row + db.perm[posB]] = sb - sc.bias;
+      out[row + db.perm[posB]] = sb;
     }
   } else {
     out[row + db.perm[posA]] = (int32_t)S;

@@ -18,10 +18,9 @@ constexpr int kMaxLanesPerChain = 32;
 struct Scoring {
   int32_t go;      // Go of Eqs. 2-3 = gap_open + gap_extend
   int32_t ge;      // Ge of Eqs. 2-3 = gap_extend
-  int32_t kbias;   // K: profile bytes hold SM + K >= 0 (pad row holds 0)
+  int32_t pad;     // profile value of pad rows and the pad residue: min(0, min SM)
   int32_t maxp;    // max(0, max SM)
-  int32_t bias;    // B: packed 16-bit lanes hold true value + B
-  int32_t thresh;  // packed lane overflows are possible only if stored S > thresh
+  int32_t thresh;  // a packed 16-bit lane may have wrapped only if its score S > thresh
 };
 
 // Per-query descriptor for the dynamic-programming kernels.
@@ -68,7 +67,8 @@ struct InterArgs {
   int32_t *out;             // [nq][out_stride] scores in caller order
   int64_t out_stride;
   int32_t *flag_count;      // packed: [nq] number of flagged sequences per query
-  int32_t *flag_pos;        // packed: [nq][out_stride] flagged sorted positions
+  int32_t *flag_pos;        // packed: [nq][flag_stride] flagged sorted positions
+  int64_t flag_stride;
   Scoring sc;
   int32_t *status;          // device status word (SW_ETIMEOUT on an expired wait)
 };
@@ -80,15 +80,25 @@ bool inter_supported_R(int R);
 size_t inter_smem_bytes(int pbuf_bytes, int threads);
 cudaError_t launch_inter(const InterArgs &a, int R, bool packed, int grid, int threads, size_t smem,
                          cudaStream_t s);
+// Raises the instantiation's shared-memory limit (plan time only) and returns resident CTAs per SM
+// (0 on failure).
 int inter_max_ctas_per_sm(int R, bool packed, int threads, size_t smem);
+
+// intra-task kernel (k_intra.cu): one CTA of intra_threads() per (query, unit) task;
+// QDesc::L = 32 * warps of the chain.
+int intra_threads();
+size_t intra_smem_bytes(int pbuf_bytes);
+cudaError_t configure_intra(int R, bool packed);  // plan time: raise the shared-memory limit
+cudaError_t launch_intra(const InterArgs &a, int R, bool packed, int grid, size_t smem, cudaStream_t s);
 
 // support kernels (k_support.cu)
 cudaError_t launch_build_profiles(const uint8_t *qres, const QDesc *qd, int32_t nq, const int8_t *submat,
-                                  int32_t kbias, uint8_t *prof, cudaStream_t s);
-// Build rescue tasks (one tile of <= chains-per-CTA flagged sequences per task) from the per-query
-// flag counts; writes the task count to *n_tasks.
+                                  int32_t pad, uint8_t *prof, cudaStream_t s);
+// Build rescue tasks from the per-query flag counts: tiles of warps_per_cta * (32 / L) flagged
+// positions (units_per_task == 0) or of units_per_task positions; flagged positions of query q
+// start at q * stride.  Writes the task count to *n_tasks and zeroes *counter.
 cudaError_t launch_rescue_tasks(const int32_t *flag_count, const QDesc *qd, int32_t nq, int64_t stride,
-                                int32_t chains_mult, Task *tasks, int32_t *n_tasks, int32_t *counter,
-                                cudaStream_t s);
+                                int32_t warps_per_cta, int32_t units_per_task, Task *tasks, int32_t *n_tasks,
+                                int32_t *counter, cudaStream_t s);
 
 }  // namespace swgb

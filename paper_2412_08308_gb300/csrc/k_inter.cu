@@ -52,7 +52,7 @@ __device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, cons
                                            uint8_t *ring, uint2 *gb, const bool prev, const bool next,
                                            const Consts &cs, Word<PACKED> &S) {
   using W = Word<PACKED>;
-  const W H0 = PACKED ? (W)cs.H0W : (W)0;
+  const W H0 = (W)0;
   const W F0 = PACKED ? (W)cs.F0W : (W)0;
   LaneState<R, PACKED> st;
   lane_reset(st, cs);
@@ -94,32 +94,39 @@ __device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, cons
       if (PACKED) rb4 = *reinterpret_cast<const uint4 *>(rres + (blk & 1) * 32 + 16);
     }
     const uint2 *gslot = rgb + (blk & 1) * 16;
+    // lane 0's columns of this block are all real or all padding (npad is a multiple of 16)
+    const bool real = blk * kColBlock < npad;
+    const bool from_strip = prev && real;
+    // 4 groups of 4 steps; only the 4 steps are unrolled, which keeps the loop
+    // body small enough for the instruction cache
+#pragma unroll 1
+    for (int g4 = 0; g4 < kColBlock / 4; ++g4) {
+      const uint32_t wa = word_of(ra4, g4), wb = word_of(rb4, g4);
 #pragma unroll
-    for (int s = 0; s < kColBlock; ++s) {
-      const int t = blk * kColBlock + s;
-      W inH = (W)__shfl_sync(0xffffffffu, outH, src);
-      W inF = (W)__shfl_sync(0xffffffffu, outF, src);
-      uint32_t inRes = __shfl_sync(0xffffffffu, outRes, src);
-      if (k == 0) {
-        const bool real = t < npad;
-        const uint32_t wa = word_of(ra4, s >> 2);
-        const uint32_t rr = PACKED ? prmt(wa, word_of(rb4, s >> 2), sel_pair(s & 3))
-                                   : prmt(wa, 0u, sel_one(s & 3));
-        inRes = real ? rr : kPadPair;
-        if (prev && real) {
-          const uint2 v = gslot[s];
-          inH = (W)v.x;
-          inF = (W)v.y;
-        } else {
-          inH = H0;
-          inF = F0;
+      for (int s4 = 0; s4 < 4; ++s4) {
+        const int s = g4 * 4 + s4;
+        const int t = blk * kColBlock + s;
+        W inH = (W)__shfl_sync(0xffffffffu, outH, src);
+        W inF = (W)__shfl_sync(0xffffffffu, outF, src);
+        uint32_t inRes = __shfl_sync(0xffffffffu, outRes, src);
+        if (k == 0) {
+          const uint32_t rr = PACKED ? prmt(wa, wb, sel_pair(s4)) : prmt(wa, 0u, sel_one(s4));
+          inRes = real ? rr : kPadPair;
+          if (from_strip) {
+            const uint2 v = gslot[s];
+            inH = (W)v.x;
+            inF = (W)v.y;
+          } else {
+            inH = H0;
+            inF = F0;
+          }
         }
-      }
-      column_step<R, PACKED>(st, prow, stride, inRes, inH, inF, cs, S, outH, outF);
-      outRes = inRes;
-      if (tail) {
-        const int j = t - (L - 1);
-        if (j >= 0 && j < npad) gb[j] = make_uint2((uint32_t)outH, (uint32_t)outF);
+        column_step<R, PACKED>(st, prow, stride, inRes, inH, inF, cs, S, outH, outF);
+        outRes = inRes;
+        if (tail) {
+          const int j = t - (L - 1);
+          if (j >= 0 && j < npad) gb[j] = make_uint2((uint32_t)outH, (uint32_t)outF);
+        }
       }
     }
     if (lead) {
@@ -193,7 +200,7 @@ __global__ void __launch_bounds__(kThreads, 2) inter_kernel(const InterArgs a) {
       if (qd.nchunks > 1) issue(1);
     }
 
-    W S = PACKED ? (W)cs.bW : (W)0;
+    W S = (W)0;
     for (int c = 0; c < qd.nchunks; ++c) {
       const int b = c & 1;
       const bool ok = mbar_wait_bounded(&mbar[b], b ? par1 : par0);
@@ -212,30 +219,32 @@ __global__ void __launch_bounds__(kThreads, 2) inter_kernel(const InterArgs a) {
     // max over the chain's lanes
     for (int d = 1; d < L; d <<= 1) S = score_max<PACKED>(S, (W)__shfl_sync(0xffffffffu, S, (k + d < L) ? lane + d : lane));
     if (live && k == 0)
-      write_scores<PACKED>(S, posA, posB, tk.q, a.db, a.sc, a.out, a.out_stride, a.flag_count, a.flag_pos);
+      write_scores<PACKED>(S, posA, posB, tk.q, a);
   }
 }
 
 template <int R, bool PACKED>
 cudaError_t launch_one(const InterArgs &a, int grid, int threads, size_t smem, cudaStream_t s) {
-  auto kern = inter_kernel<R, PACKED>;
-  static bool configured = false;  // per instantiation; max dynamic smem of this library is < 200 KB
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
-  kern<<<grid, threads, smem, s>>>(a);
+  inter_kernel<R, PACKED><<<grid, threads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
+// Raise the dynamic shared-memory limit of an instantiation (done at plan time,
+// never inside a launch sequence that may be captured into a graph) and return
+// its resident CTAs per SM for the given block size and shared memory.
 template <int R, bool PACKED>
-int occupancy_one(int threads, size_t smem) {
-  int n = 0;
+int configure_one(int threads, size_t smem) {
   auto kern = inter_kernel<R, PACKED>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem) != cudaSuccess) return 1;
-  return n > 0 ? n : 1;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
 }
 
 }  // namespace
@@ -249,7 +258,7 @@ size_t inter_smem_bytes(int pbuf_bytes, int threads) {
   return 128 + 2 * (size_t)pbuf_bytes + (size_t)(threads / 32) * kChainsPerWarpMax * kRingBytes;
 }
 
-#define SWGB_INTER_R_LIST(X) X(8) X(12) X(16) X(24)
+#define SWGB_INTER_R_LIST(X) X(4) X(8) X(12) X(16) X(24)
 
 bool inter_supported_R(int R) {
 #define SWGB_CASE(RR) if (R == RR) return true;
@@ -270,7 +279,7 @@ cudaError_t launch_inter(const InterArgs &a, int R, bool packed, int grid, int t
 
 int inter_max_ctas_per_sm(int R, bool packed, int threads, size_t smem) {
 #define SWGB_CASE(RR) \
-  if (R == RR) return packed ? occupancy_one<RR, true>(threads, smem) : occupancy_one<RR, false>(threads, smem);
+  if (R == RR) return packed ? configure_one<RR, true>(threads, smem) : configure_one<RR, false>(threads, smem);
   SWGB_INTER_R_LIST(SWGB_CASE)
 #undef SWGB_CASE
   return 1;

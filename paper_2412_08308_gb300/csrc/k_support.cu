@@ -5,13 +5,13 @@ namespace swgb {
 namespace {
 
 // Query profile (Sec. 2.2: the SM(Q[i], D[j]) term of Eq. 1, tabulated per
-// database residue): byte P[c][i] = SM(Q[i], c) + K for residue c = 0..19 and
-// query row i; the pad residue (c = 20) and rows past the query end hold 0,
-// i.e. the most negative score -K.  Layout per query: nchunks chunks, each
+// database residue): signed byte P[c][i] = SM(Q[i], c) for residue c = 0..19
+// and query row i; the pad residue (c = 20) and rows past the query end hold
+// `pad` = min(0, min SM).  Layout per query: nchunks chunks, each
 // [21][chunk_stride] bytes, chunk c covering rows c*L*R .. c*L*R + L*R - 1 at
-// byte offsets 0 .. L*R-1 of each residue row; bytes past L*R are 0.
+// byte offsets 0 .. L*R-1 of each residue row; bytes past L*R hold `pad` too.
 __global__ void build_profiles_kernel(const uint8_t *__restrict__ qres, const QDesc *__restrict__ qd,
-                                      const int8_t *__restrict__ submat, int32_t kbias,
+                                      const int8_t *__restrict__ submat, int32_t pad,
                                       uint8_t *__restrict__ prof) {
   __shared__ int8_t sm[kAlphabet * kAlphabet];
   for (int i = threadIdx.x; i < kAlphabet * kAlphabet; i += blockDim.x) sm[i] = submat[i];
@@ -32,9 +32,9 @@ __global__ void build_profiles_kernel(const uint8_t *__restrict__ qres, const QD
     for (int b = 0; b < 4; ++b) {
       const int xx = xb + b;
       const int row = c * LR + xx;
-      uint32_t byte = 0;
-      if (xx < LR && row < d.m && rho < kAlphabet) byte = (uint32_t)(sm[q[row] * kAlphabet + rho] + kbias);
-      v |= byte << (8 * b);
+      int32_t val = pad;
+      if (xx < LR && row < d.m && rho < kAlphabet) val = sm[q[row] * kAlphabet + rho];
+      v |= ((uint32_t)val & 0xffu) << (8 * b);
     }
     out[w] = v;
   }
@@ -42,7 +42,8 @@ __global__ void build_profiles_kernel(const uint8_t *__restrict__ qres, const QD
 
 // One task per tile of up to chains-per-CTA flagged sequences of one query.
 __global__ void rescue_tasks_kernel(const int32_t *__restrict__ flag_count, const QDesc *__restrict__ qd,
-                                    int32_t nq, int64_t stride, int32_t warps_per_cta, Task *__restrict__ tasks,
+                                    int32_t nq, int64_t stride, int32_t warps_per_cta, int32_t units_per_task,
+                                    Task *__restrict__ tasks,
                                     int32_t *__restrict__ n_tasks, int32_t *__restrict__ counter) {
   __shared__ int32_t part[1024];
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -50,7 +51,7 @@ __global__ void rescue_tasks_kernel(const int32_t *__restrict__ flag_count, cons
   const int q0 = min(nq, tid * per), q1 = min(nq, q0 + per);
   int32_t mine = 0;
   for (int q = q0; q < q1; ++q) {
-    const int chains = warps_per_cta * (32 / qd[q].L);
+    const int chains = units_per_task > 0 ? units_per_task : warps_per_cta * (32 / qd[q].L);
     mine += (flag_count[q] + chains - 1) / chains;
   }
   part[tid] = mine;
@@ -63,7 +64,7 @@ __global__ void rescue_tasks_kernel(const int32_t *__restrict__ flag_count, cons
   }
   int32_t base = part[tid] - mine;
   for (int q = q0; q < q1; ++q) {
-    const int chains = warps_per_cta * (32 / qd[q].L);
+    const int chains = units_per_task > 0 ? units_per_task : warps_per_cta * (32 / qd[q].L);
     const int cnt = flag_count[q];
     for (int t0 = 0; t0 < cnt; t0 += chains) {
       Task tk;
@@ -83,13 +84,13 @@ __global__ void rescue_tasks_kernel(const int32_t *__restrict__ flag_count, cons
 }  // namespace
 
 cudaError_t launch_build_profiles(const uint8_t *qres, const QDesc *qd, int32_t nq, const int8_t *submat,
-                                  int32_t kbias, uint8_t *prof, cudaStream_t s) {
+                                  int32_t pad, uint8_t *prof, cudaStream_t s) {
   if (nq <= 0) return cudaSuccess;
   int64_t done = 0;
   while (done < nq) {  // grid.y is limited to 65535
     const int chunk = (int)std::min<int64_t>(65535, nq - done);
     dim3 grid(8, chunk);
-    build_profiles_kernel<<<grid, 256, 0, s>>>(qres, qd + done, submat, kbias, prof);
+    build_profiles_kernel<<<grid, 256, 0, s>>>(qres, qd + done, submat, pad, prof);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     done += chunk;
@@ -98,9 +99,10 @@ cudaError_t launch_build_profiles(const uint8_t *qres, const QDesc *qd, int32_t 
 }
 
 cudaError_t launch_rescue_tasks(const int32_t *flag_count, const QDesc *qd, int32_t nq, int64_t stride,
-                                int32_t warps_per_cta, Task *tasks, int32_t *n_tasks, int32_t *counter,
-                                cudaStream_t s) {
-  rescue_tasks_kernel<<<1, 1024, 0, s>>>(flag_count, qd, nq, stride, warps_per_cta, tasks, n_tasks, counter);
+                                int32_t warps_per_cta, int32_t units_per_task, Task *tasks, int32_t *n_tasks,
+                                int32_t *counter, cudaStream_t s) {
+  rescue_tasks_kernel<<<1, 1024, 0, s>>>(flag_count, qd, nq, stride, warps_per_cta, units_per_task, tasks, n_tasks,
+                                         counter);
   return cudaGetLastError();
 }
 

@@ -29,10 +29,16 @@ def api():
     return _api
 
 
-def _search(api, db_seqs, q_seqs, mode, sm=BLOSUM62, go=10, ge=2):
+def _search(api, db_seqs, q_seqs, mode, sm=BLOSUM62, go=10, ge=2, opts=None):
     db = api.Database.from_sequences(db_seqs)
     try:
-        return api.search(db, q_seqs.residues, q_seqs.offsets, sm, go, ge, mode)
+        if opts is None:
+            return api.search(db, q_seqs.residues, q_seqs.offsets, sm, go, ge, mode)
+        pq = api.PreparedQueries(db, q_seqs.residues, q_seqs.offsets, sm, go, ge, mode, opts=opts)
+        out = pq.search().cpu().numpy()
+        pq.status()
+        pq.close()
+        return out
     finally:
         db.close()
 
@@ -65,14 +71,12 @@ def _ragged(seed, n_db, n_q, qmax):
 
 
 @pytest.mark.parametrize("mode", MODES)
-@pytest.mark.parametrize("R,L", [(16, 0), (8, 4), (12, 5), (24, 13), (16, 32), (8, 31)])
-def test_ragged_tiles(api, monkeypatch, mode, R, L):
+@pytest.mark.parametrize("R,L", [(16, 0), (8, 4), (12, 5), (24, 13), (16, 32), (8, 31), (4, 9), (4, 0)])
+def test_ragged_tiles(api, mode, R, L):
     # database lengths straddling every padding boundary, empty and 1-residue
     # sequences, queries from 0 residues to several chunks of L*R rows
-    monkeypatch.setenv("SWGB_R", str(R))
-    monkeypatch.setenv("SWGB_L", str(L))
     db, q = _ragged(10 + R + L, 301, 9, 900)
-    got = _search(api, db, q, mode)
+    got = _search(api, db, q, mode, opts=api.options(rows_per_lane=R, lanes_per_chain=L))
     _assert_equal(got, oracle.scores(q, db, BLOSUM62, 10, 2))
 
 
@@ -117,19 +121,30 @@ def test_packed_overflow_is_rescued_exactly(api):
     pq.close()
 
 
-@pytest.mark.parametrize("mode", MODES)
-def test_config3_precision_path(api, mode):
-    # config 1's database plus 10 planted ~8,000-residue homologs of an
-    # 8,000-residue query; their int16 scores overflow and are rescued
+@pytest.fixture(scope="module")
+def config3():
     w = make_config(3)
-    exp = oracle.scores(w["queries"], w["db"], BLOSUM62, 10, 2)
-    assert exp[1, w["homolog_ids"]].min() > 32767
+    w["expected"] = oracle.scores(w["queries"], w["db"], BLOSUM62, 10, 2)
+    assert w["expected"][1, w["homolog_ids"]].min() > 32767
+    return w
+
+
+@pytest.mark.parametrize("mode,cutover", [("int32", 0), ("packed", 0), ("packed", 16384)])
+def test_config3_precision_path(api, config3, mode, cutover):
+    # config 1's database plus 10 planted ~8,000-residue homologs of an
+    # 8,000-residue query, whose scores exceed the 16-bit range.  With the
+    # default cutover the homologs run in the intra-task kernel, which takes
+    # them straight to int32 (their bound max(SM)*min(m, n) passes the 16-bit
+    # threshold); with cutover 16384 they run packed in the inter-task kernel,
+    # saturate, are flagged and rescued exactly.
+    w = config3
     db = api.Database.from_sequences(w["db"])
-    pq = api.PreparedQueries(db, w["queries"].residues, w["queries"].offsets, BLOSUM62, 10, 2, mode)
+    pq = api.PreparedQueries(db, w["queries"].residues, w["queries"].offsets, BLOSUM62, 10, 2, mode,
+                             opts=api.options(cutover=cutover))
     got = pq.search().cpu().numpy()
     rescued = pq.status()
-    _assert_equal(got, exp)
-    if mode == "packed":
+    _assert_equal(got, w["expected"])
+    if mode == "packed" and cutover == 16384:
         assert rescued >= len(w["homolog_ids"])
     pq.close()
     db.close()
@@ -209,4 +224,115 @@ def test_invalid_arguments_rejected(api):
     sm[0, 0] = 100
     with pytest.raises(SwError):
         api.search(db, q.residues, q.offsets, sm, 10, 2, "packed")
+    db.close()
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("intra_rows", [8, 16])
+def test_intra_task_kernel(api, mode, intra_rows):
+    # database sequences from 1 to ~5,000 residues with the cutover at 1,000:
+    # the long ones go to the multi-warp intra-task kernel, concurrently with
+    # the inter-task kernel; queries up to 9,000 residues span several chunks
+    # of 32 * 16 * intra_rows rows
+    rng = np.random.Generator(np.random.PCG64(40 + intra_rows))
+    lens = [1, 15, 16, 17, 999, 1000, 1001, 1007, 2048, 4999] + list(rng.integers(1, 5000, size=40))
+    db = from_list([rng.integers(0, 20, size=int(L)).astype(np.uint8) for L in lens])
+    ql = [0, 1, 33, 511, 512, 513, 3000, 4097, 9000]
+    q = from_list([rng.integers(0, 20, size=int(L)).astype(np.uint8) for L in ql])
+    got = _search(api, db, q, mode, opts=api.options(cutover=1000, intra_rows=intra_rows))
+    _assert_equal(got, oracle.scores(q, db, BLOSUM62, 10, 2))
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_everything_intra(api, mode):
+    # cutover 1: every unit goes through the intra-task kernel
+    db, q = _ragged(91, 60, 5, 700)
+    got = _search(api, db, q, mode, opts=api.options(cutover=1))
+    _assert_equal(got, oracle.scores(q, db, BLOSUM62, 10, 2))
+
+
+def test_intra_saturating_units_exact(api):
+    # long self-matches above the 16-bit range on intra-task units (routed to
+    # int32) next to short ones that saturate in the packed inter-task kernel
+    rng = np.random.Generator(np.random.PCG64(17))
+    sm = np.full((20, 20), -5, dtype=np.int8)
+    np.fill_diagonal(sm, 40)
+    base = rng.integers(0, 20, size=3000).astype(np.uint8)
+    seqs = [rng.integers(0, 20, size=int(rng.integers(100, 3000))).astype(np.uint8) for _ in range(30)]
+    seqs[5], seqs[6], seqs[20] = base.copy(), base[:2500].copy(), base[500:].copy()
+    seqs[21], seqs[22] = base[:900].copy(), base[1000:1950].copy()
+    db = from_list(seqs)
+    q = from_list([base, base[:1000]])
+    exp = oracle.scores(q, db, sm, 10, 2)
+    assert exp.max() > 32767
+    dbh = api.Database.from_sequences(db)
+    pq = api.PreparedQueries(dbh, q.residues, q.offsets, sm, 10, 2, "packed", opts=api.options(cutover=1000))
+    got = pq.search().cpu().numpy()
+    rescued = pq.status()
+    _assert_equal(got, exp)
+    assert rescued >= 2  # the two short self-matches (900 and 950 residues x 40 > 32767)
+    pq.close()
+    dbh.close()
+
+
+def test_bad_options_rejected(api):
+    from paper_2412_08308_gb300._native import SW_EINVAL, SwError
+
+    db_s = random_sequences(37, 10, 50, 0.5, 1, 100)
+    q = random_sequences(38, 2, 50, 0.5, 1, 100)
+    db = api.Database.from_sequences(db_s)
+    for opts in (api.options(rows_per_lane=7), api.options(lanes_per_chain=3), api.options(intra_rows=12)):
+        with pytest.raises(SwError) as e:
+            api.PreparedQueries(db, q.residues, q.offsets, BLOSUM62, 10, 2, "packed", opts=opts)
+        assert e.value.code == SW_EINVAL
+    db.close()
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_graph_replay_matches(api, mode):
+    # the whole search captured in a CUDA graph (long units included, so the
+    # side-stream fork/join is captured too) and replayed twice, then again
+    # into a different output buffer (re-capture)
+    import torch
+
+    rng = np.random.Generator(np.random.PCG64(61))
+    lens = list(rng.integers(1, 600, size=120)) + [2500, 3100]
+    db_s = from_list([rng.integers(0, 20, size=int(L)).astype(np.uint8) for L in lens])
+    q_s = random_sequences(62, 5, 300, 0.5, 1, 1500)
+    exp = oracle.scores(q_s, db_s, BLOSUM62, 10, 2)
+    db = api.Database.from_sequences(db_s)
+    pq = api.PreparedQueries(db, q_s.residues, q_s.offsets, BLOSUM62, 10, 2, mode, opts=api.options(cutover=2048))
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        out = torch.full((len(q_s), len(db_s)), -1, dtype=torch.int32, device="cuda")
+        for _ in range(2):
+            pq.search_graph(out, stream=st)
+            st.synchronize()
+            _assert_equal(out.cpu().numpy(), exp)
+            out.fill_(-1)
+        out2 = torch.full_like(out, -1)
+        pq.search_graph(out2, stream=st)
+        st.synchronize()
+        _assert_equal(out2.cpu().numpy(), exp)
+    assert pq.status(stream=st) >= 0
+    pq.close()
+    db.close()
+
+
+def test_autotuner_picks_a_correct_plan(api, tmp_path):
+    from paper_2412_08308_gb300 import tune
+
+    db_s = random_sequences(81, 4000, 300, 0.5, 20, 1000)
+    q_s = random_sequences(82, 12, 350, 0.5, 50, 2000)
+    db = api.Database.from_sequences(db_s)
+    cache = str(tmp_path / "tune.json")
+    opts, table = tune.tune(db, db_s.lengths, q_s.residues, q_s.offsets, BLOSUM62, rows=(4, 16), cutovers=(512, 2048),
+                            reps=1, cache_path=cache)
+    assert len(table) == 4 and all(g > 0 for _, _, g in table)
+    assert (opts.rows_per_lane, opts.cutover) in [(r, c) for r, c, _ in table]
+    again, table2 = tune.tune(db, db_s.lengths, q_s.residues, q_s.offsets, BLOSUM62, rows=(4, 16),
+                              cutovers=(512, 2048), reps=1, cache_path=cache)
+    assert (again.rows_per_lane, again.cutover) == (opts.rows_per_lane, opts.cutover)  # from the cache
+    got = _search(api, db_s, q_s, "packed", opts=opts)
+    _assert_equal(got, oracle.scores(q_s, db_s, BLOSUM62, 10, 2))
     db.close()

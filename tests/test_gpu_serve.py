@@ -1,0 +1,60 @@
+"""Serving path: continuous batching over a resident database.
+
+Requests arrive while earlier batches are still on the GPU; each result must
+equal the same query searched alone (and the CPU oracle)."""
+
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from workload import random_sequences
+from workload.matrices import BLOSUM62
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2412_08308_gb300 import api as _api
+    from paper_2412_08308_gb300 import build
+
+    build()
+    oracle.build()
+    return _api
+
+
+@pytest.mark.parametrize("mode", ["packed", "int32"])
+def test_results_same_alone_and_in_the_mix(api, mode):
+    from paper_2412_08308_gb300.serve import Server
+
+    db_s = random_sequences(71, 3000, 300, 0.5, 20, 1000)
+    qs = random_sequences(72, 40, 300, 0.5, 30, 1500)
+    db = api.Database.from_sequences(db_s)
+    alone = [api.search(db, qs[i], np.array([0, len(qs[i])]), BLOSUM62, 10, 2, mode)[0] for i in range(len(qs))]
+    srv = Server(db, BLOSUM62, 10, 2, mode, max_batch=6, n_streams=3)
+    futs = []
+    # bursts from two client threads, so batches overlap on the device
+    def client(lo, hi):
+        for i in range(lo, hi):
+            futs.append((i, srv.submit(qs[i])))
+            if i % 7 == 0:
+                time.sleep(0.002)
+    t1 = threading.Thread(target=client, args=(0, 20))
+    t2 = threading.Thread(target=client, args=(20, 40))
+    t1.start(); t2.start(); t1.join(); t2.join()
+    got = {i: f.result(timeout=120) for i, f in futs}
+    srv.close()
+    for i in range(len(qs)):
+        np.testing.assert_array_equal(got[i], alone[i])
+    exp = oracle.scores(qs.subset(range(5)), db_s, BLOSUM62, 10, 2)
+    for i in range(5):
+        np.testing.assert_array_equal(got[i], exp[i])
+    st = srv.latency_stats()
+    assert st["requests"] == len(qs) and st["p99_ms"] >= st["p50_ms"] > 0
+    db.close()
