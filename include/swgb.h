@@ -196,6 +196,39 @@ int sw_search(const sw_db *db, const uint8_t *queries, const int64_t *q_offsets,
               const int8_t *submat, int32_t gap_open, int32_t gap_extend, int32_t mode,
               int32_t *scores_out, void *stream);
 
+/*
+ * sw_search_noalloc -- score one query against a prepared database without
+ * allocating any memory.  (The paper has no counterpart: this serves callers
+ * that cannot allocate device memory while they search -- a service that fixes
+ * its memory budget at start-up, a real-time loop in which a cudaMalloc could
+ * synchronise the device and stall every stream, a host that runs the library
+ * inside an arena it does not control.)
+ *
+ * Every scratch buffer the search needs lives in one 16 MiB static device
+ * array that each GPU loading this library holds until the process exits;
+ * the call makes no cudaMalloc or cudaFree and calls no allocating library
+ * routine.  It computes exact int32 scores with the inter-task kernel and
+ * returns after they are in place (it synchronises `stream`).
+ *
+ *   db          a prepared database on the calling thread's current device
+ *   query, m    host pointer to m residue codes 0..19, 0 <= m <= 768
+ *   submat      host pointer, 20x20 int8; gap_open, gap_extend as sw_search
+ *   scores_dev  DEVICE pointer to n_db int32, written in the caller's order
+ *   stream      stream for the work (NULL = legacy default stream)
+ *
+ * Limits: queries of at most 768 residues, databases of at most 2,000,000
+ * sequences; larger sizes are rejected with SW_EINVAL and a message.
+ * The first call on a device looks up the device address of the scratch
+ * array and configures the kernel; make that first call before any CUDA
+ * stream capture on that device.  All calls on a device share the array and
+ * it keeps the previous call's contents: calls whose GPU work could overlap
+ * (from several host threads, or on several streams) race and must be
+ * serialised by the caller.
+ * Errors: SW_EINVAL, SW_ECUDA, SW_ETIMEOUT.
+ */
+int sw_search_noalloc(const sw_db *db, const uint8_t *query, int64_t m, const int8_t *submat,
+                      int32_t gap_open, int32_t gap_extend, int32_t *scores_dev, void *stream);
+
 /* Message for the last failed call on this thread ("" if none). */
 const char *sw_last_error(void);
 

@@ -31,6 +31,7 @@ SIGNATURES = {
     "sw_queries_set_timing": (ctypes.c_int, [_p, _i32]),
     "sw_queries_kernel_ms": (ctypes.c_int, [_p, _p, ctypes.POINTER(ctypes.c_float)]),
     "sw_queries_info": (ctypes.c_int, [_p, _pi64, _pi64, _pi64, _pi64]),
+    "sw_search_noalloc": (ctypes.c_int, [_p, _p, _i64, _p, _i32, _i32, _p, _p]),
     "sw_last_error": (ctypes.c_char_p, []),
 }
 
@@ -140,3 +141,7 @@ def sw_queries_info(qh):
 
 def sw_search_graph(db, qh, scores_dev_ptr, stream):
     return check(lib().sw_search_graph(db, qh, scores_dev_ptr, stream))
+
+
+def sw_search_noalloc(db, q_ptr, m, submat_ptr, gap_open, gap_extend, scores_dev_ptr, stream):
+    return check(lib().sw_search_noalloc(db, q_ptr, m, submat_ptr, gap_open, gap_extend, scores_dev_ptr, stream))

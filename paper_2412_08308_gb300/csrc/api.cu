@@ -167,6 +167,13 @@ void free_queries(sw_queries *q) {
 
 }  // namespace
 
+namespace swgb {
+const DbView &db_view(const sw_db *db) { return db->view; }
+int db_device(const sw_db *db) { return db->device; }
+int set_last_error(int code, const char *msg) { return fail(code, "%s", msg); }
+void clear_last_error() { g_err.clear(); }
+}  // namespace swgb
+
 extern "C" {
 
 const char *sw_last_error(void) { return g_err.c_str(); }

@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+struct sw_db;
+
 namespace swgb {
 
 constexpr int kAlphabet = 20;      // residue codes 0..19
@@ -100,5 +102,12 @@ cudaError_t launch_build_profiles(const uint8_t *qres, const QDesc *qd, int32_t 
 cudaError_t launch_rescue_tasks(const int32_t *flag_count, const QDesc *qd, int32_t nq, int64_t stride,
                                 int32_t warps_per_cta, int32_t units_per_task, Task *tasks, int32_t *n_tasks,
                                 int32_t *counter, cudaStream_t s);
+
+// Accessors for translation units other than api.cu (the sw_db layout is private to it).
+const DbView &db_view(const struct ::sw_db *db);
+int db_device(const struct ::sw_db *db);
+// Record the thread's last error message (see sw_last_error) and return `code`.
+int set_last_error(int code, const char *msg);
+void clear_last_error();
 
 }  // namespace swgb
