@@ -53,10 +53,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--workload", default="twenty_queries_vs_200k",
+                    help="named synthetic workload (workload.gen.WORKLOADS)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the int32 and small-config side measurements")
+    ap.add_argument("--no-extras", action="store_true", help="skip the int32 and small-workload side measurements")
     ap.add_argument("--serve-requests", type=int, default=600,
                     help="requests of the serving run (Poisson 50/s, 500,000-protein database); 0 skips it")
     ap.add_argument("--mode", default="packed", choices=["packed", "int32"], help="form of the timed search")
@@ -244,7 +245,7 @@ def time_prepared(pq, out, steps, flush, timing=False):
 
 
 def run_serving(n_requests, mode):
-    """Continuous-batching serving run on the config-5 shape: 500,000 synthetic
+    """Continuous-batching serving run on the serving_500k workload: 500,000 synthetic
     proteins (~180M residues) resident in HBM, queries (median 400, 30-3000)
     arriving as a Poisson process at 50/s.  Reports latency percentiles and
     offered vs sustained GCUPS over the first n_requests arrivals."""
@@ -252,10 +253,10 @@ def run_serving(n_requests, mode):
 
     from paper_2412_08308_gb300 import api
     from paper_2412_08308_gb300.serve import Server
-    from workload import make_config
+    from workload import make_workload
     from workload.matrices import BLOSUM62
 
-    w = make_config(5, n_queries=n_requests)
+    w = make_workload("serving_500k", n_queries=n_requests)
     db = api.Database.from_sequences(w["db"])
     q = w["queries"]
     arrivals = w["arrivals"]
@@ -349,9 +350,9 @@ def run_ours(args, w):
         extras["packed_over_int32"] = round(value / world / extras["int32_gcups"], 3)
         pq32.close()
         # the small single-query workload (1 query of 144 aa x 2,000 proteins)
-        from workload import make_config
+        from workload import make_workload
 
-        w1 = make_config(1)
+        w1 = make_workload("one_query_vs_2k")
         db1 = api.Database.from_sequences(w1["db"])
         c1 = float(w1["queries"].total) * float(w1["db"].total)
         out1 = torch.empty((1, len(w1["db"])), dtype=torch.int32, device="cuda")
@@ -364,7 +365,7 @@ def run_ours(args, w):
             g1[mode] = c1 / float(np.median(ts)) / 1e9
             p1.close()
         db1.close()
-        extras["config1_1x144_vs_2000"] = {"packed_gcups": round(g1["packed"], 1), "int32_gcups": round(g1["int32"], 1),
+        extras["one_query_vs_2k"] = {"packed_gcups": round(g1["packed"], 1), "int32_gcups": round(g1["int32"], 1),
                                            "ratio": round(g1["packed"] / g1["int32"], 3)}
 
     # end to end through sw_search with host buffers
@@ -418,9 +419,9 @@ def run_ours(args, w):
 
 def main():
     args = parse()
-    from workload import make_config
+    from workload import make_workload
 
-    w = make_config(args.config)
+    w = make_workload(args.workload)
     if args.queries:
         w["queries"] = w["queries"].subset(range(min(args.queries, len(w["queries"]))))
     if args.db_limit:

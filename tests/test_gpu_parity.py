@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
-from workload import from_list, make_config, random_sequences, sample_indices
+from workload import from_list, make_workload, random_sequences, sample_indices
 from workload.matrices import BLOSUM62
 
 pytestmark = pytest.mark.gpu
@@ -52,9 +52,9 @@ def _assert_equal(got, exp):
 
 
 @pytest.mark.parametrize("mode", MODES)
-def test_config1_full(api, mode):
+def test_one_query_vs_2k_full(api, mode):
     # 1 query of 144 residues against 2,000 synthetic proteins
-    w = make_config(1)
+    w = make_workload("one_query_vs_2k")
     got = _search(api, w["db"], w["queries"], mode)
     _assert_equal(got, oracle.scores(w["queries"], w["db"], BLOSUM62, 10, 2))
 
@@ -122,22 +122,22 @@ def test_packed_overflow_is_rescued_exactly(api):
 
 
 @pytest.fixture(scope="module")
-def config3():
-    w = make_config(3)
+def homologs():
+    w = make_workload("homologs_8k")
     w["expected"] = oracle.scores(w["queries"], w["db"], BLOSUM62, 10, 2)
     assert w["expected"][1, w["homolog_ids"]].min() > 32767
     return w
 
 
 @pytest.mark.parametrize("mode,cutover", [("int32", 0), ("packed", 0), ("packed", 16384)])
-def test_config3_precision_path(api, config3, mode, cutover):
-    # config 1's database plus 10 planted ~8,000-residue homologs of an
+def test_homologs_precision_path(api, homologs, mode, cutover):
+    # the 2,000-protein database plus 10 planted ~8,000-residue homologs of an
     # 8,000-residue query, whose scores exceed the 16-bit range.  With the
     # default cutover the homologs run in the intra-task kernel, which takes
     # them straight to int32 (their bound max(SM)*min(m, n) passes the 16-bit
     # threshold); with cutover 16384 they run packed in the inter-task kernel,
     # saturate, are flagged and rescued exactly.
-    w = config3
+    w = homologs
     db = api.Database.from_sequences(w["db"])
     pq = api.PreparedQueries(db, w["queries"].residues, w["queries"].offsets, BLOSUM62, 10, 2, mode,
                              opts=api.options(cutover=cutover))
@@ -151,10 +151,10 @@ def test_config3_precision_path(api, config3, mode, cutover):
 
 
 @pytest.mark.parametrize("mode", MODES)
-def test_config2_sampled(api, mode):
+def test_twenty_queries_vs_200k_sampled(api, mode):
     # 20 queries (144..5478) against 200,000 sequences; every score of a
     # seeded 300-sequence sample is compared with the oracle
-    w = make_config(2)
+    w = make_workload("twenty_queries_vs_200k")
     got = _search(api, w["db"], w["queries"], mode)
     idx = sample_indices(len(w["db"]), 300)
     exp = oracle.scores(w["queries"], w["db"], BLOSUM62, 10, 2, subset=idx)
@@ -162,10 +162,10 @@ def test_config2_sampled(api, mode):
     assert got.min() >= 0
 
 
-def test_config4_sampled(api):
+def test_thousand_queries_vs_50k_sampled(api):
     # 1,000 queries against 50,000 sequences (packed); a sample of 12 queries
     # x 150 sequences is checked
-    w = make_config(4)
+    w = make_workload("thousand_queries_vs_50k")
     got = _search(api, w["db"], w["queries"], "packed")
     qi = sample_indices(len(w["queries"]), 12, seed=4101)
     di = sample_indices(len(w["db"]), 150, seed=4102)

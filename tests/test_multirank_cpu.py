@@ -32,7 +32,7 @@ def _worker(rank, world, port, outdir):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
                       LOCAL_RANK=str(rank))
     import bench
-    from workload import make_config
+    from workload import make_workload
 
     args = SimpleNamespace(impl="reference", gpus=world, steps=1, warmup=0)
     world_, rank_, local_, pg = bench.dist_setup(args)
@@ -42,7 +42,7 @@ def _worker(rank, world, port, outdir):
     res = {"max": t}
     pg.destroy_process_group()
     # reference arm: rank 0 prints one JSON line, the others return silently
-    w = make_config(1, n_db=40)
+    w = make_workload("one_query_vs_2k", n_db=40)
     os.environ.update(MASTER_PORT=str(port + 1))
     buf = io.StringIO()
     with redirect_stdout(buf):

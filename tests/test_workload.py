@@ -1,8 +1,8 @@
-"""The seeded synthetic workloads have the shapes the benchmark configs name."""
+"""The seeded synthetic workloads have the shapes their names and descriptions state."""
 
 import numpy as np
 
-from workload import gen, make_config, mutate, random_sequences
+from workload import gen, make_workload, mutate, random_sequences
 
 
 def test_generator_is_deterministic():
@@ -14,21 +14,21 @@ def test_generator_is_deterministic():
     assert L.min() >= 20 and L.max() <= 1000
 
 
-def test_config_shapes_small():
-    w1 = make_config(1)
+def test_workload_shapes_small():
+    w1 = make_workload("one_query_vs_2k")
     assert len(w1["db"]) == 2000 and w1["queries"].lengths.tolist() == [144]
     cells = w1["db"].total * 144
     assert 0.8e8 < cells < 1.2e8  # "~1e8 cells"
-    assert gen.config2_query_lengths()[0] == 144 and gen.config2_query_lengths()[-1] == 5478
-    w3 = make_config(3)
+    assert gen.twenty_query_lengths()[0] == 144 and gen.twenty_query_lengths()[-1] == 5478
+    w3 = make_workload("homologs_8k")
     assert len(w3["db"]) == 2010 and w3["queries"].lengths.tolist() == [144, 8000]
     assert len(w3["homolog_ids"]) == 10
     for i in w3["homolog_ids"]:
         assert 7500 < len(w3["db"][int(i)]) < 8500
-    w4 = make_config(4, n_db=1000, n_queries=50)
+    w4 = make_workload("thousand_queries_vs_50k", n_db=1000, n_queries=50)
     assert len(w4["queries"]) == 50
     assert w4["queries"].lengths.min() >= 50 and w4["queries"].lengths.max() <= 2000
-    w5 = make_config(5, n_db=1000, n_queries=100)
+    w5 = make_workload("serving_500k", n_db=1000, n_queries=100)
     arr = w5["arrivals"]
     assert (np.diff(arr) > 0).all() and 0.5 < arr[-1] / 100 * 50 < 2.0
 

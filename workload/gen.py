@@ -130,7 +130,7 @@ def mutate(rng, seq, p_sub=0.10, p_indel=0.01):
 
 
 # ---------------------------------------------------------------------------
-# The five benchmark workloads.
+# The five benchmark workloads, by name.
 # ---------------------------------------------------------------------------
 
 DB_SEED = 1000
@@ -138,25 +138,38 @@ QUERY_SEED = 2000
 ARRIVAL_SEED = 3000
 SAMPLE_SEED = 4000
 
+WORKLOADS = {
+    "one_query_vs_2k": "1 query of 144 residues x 2,000 proteins (~1e8 cells)",
+    "twenty_queries_vs_200k": "20 queries of 144..5478 residues (log-uniform) x 200,000 proteins (~67.5M residues)",
+    "homologs_8k": "2,000 proteins + 10 planted ~8,000-residue homologs of an 8,000-residue query; "
+                   "queries: the 144-residue query and the 8,000-residue source",
+    "thousand_queries_vs_50k": "1,000 queries (median 350, 50..2000) x 50,000 proteins",
+    "serving_500k": "500,000 proteins (~180M residues); 10,000 queries (median 400, 30..3000) arriving "
+                    "as a Poisson process at 50/s",
+}
 
-def config2_query_lengths():
+
+def twenty_query_lengths():
     """20 query lengths spread log-uniformly over 144..5478 residues."""
     return [int(round(144 * (5478 / 144) ** (k / 19))) for k in range(20)]
 
 
-def make_config(k, n_db=None, n_queries=None):
-    """Build workload ``k`` (1..5).
+def make_workload(name, n_db=None, n_queries=None):
+    """Build a named workload (see WORKLOADS).
 
     Returns a dict with ``db`` (Sequences), ``queries`` (Sequences) and, where
-    the workload has them, ``homolog_ids`` (config 3) or ``arrivals`` (config 5,
-    seconds).  ``n_db`` / ``n_queries`` shrink the workload (tests only).
+    the workload has them, ``homolog_ids`` (homologs_8k) or ``arrivals``
+    (serving_500k, seconds).  ``n_db`` / ``n_queries`` shrink it (tests only).
+    Seeds: database 1000 + k, queries 2000 + k, k = 1..5 in the order above.
     """
-    out = {"config": k}
-    if k in (1, 3):
+    if name not in WORKLOADS:
+        raise ValueError(f"unknown workload {name!r}; one of {sorted(WORKLOADS)}")
+    out = {"name": name}
+    if name in ("one_query_vs_2k", "homologs_8k"):
         db = random_sequences(DB_SEED + 1, n_db or 2000, 300, 0.5, 20, 1000)
         rng = np.random.Generator(np.random.PCG64(QUERY_SEED + 1))
         q144 = random_sequence(rng, 144)
-        if k == 1:
+        if name == "one_query_vs_2k":
             out.update(db=db, queries=from_list([q144]))
             return out
         rng3 = np.random.Generator(np.random.PCG64(QUERY_SEED + 3))
@@ -175,28 +188,26 @@ def make_config(k, n_db=None, n_queries=None):
                 si += 1
         out.update(db=from_list(merged), queries=from_list([q144, src]), homolog_ids=pos.astype(np.int64))
         return out
-    if k == 2:
+    if name == "twenty_queries_vs_200k":
         db = random_sequences(DB_SEED + 2, n_db or 200_000, 300, 0.5, 20, 1000)
         rng = np.random.Generator(np.random.PCG64(QUERY_SEED + 2))
-        lens = config2_query_lengths()
+        lens = twenty_query_lengths()
         if n_queries:
             lens = lens[:n_queries]
         out.update(db=db, queries=from_list([random_sequence(rng, m) for m in lens]))
         return out
-    if k == 4:
+    if name == "thousand_queries_vs_50k":
         db = random_sequences(DB_SEED + 4, n_db or 50_000, 300, 0.5, 20, 1000)
         q = random_sequences(QUERY_SEED + 4, n_queries or 1000, 350, 0.5, 50, 2000)
         out.update(db=db, queries=q)
         return out
-    if k == 5:
-        db = random_sequences(DB_SEED + 5, n_db or 500_000, 300, 0.65, 20, 1000)
-        nq = n_queries or 10_000
-        q = random_sequences(QUERY_SEED + 5, nq, 400, 0.5, 30, 3000)
-        rng = np.random.Generator(np.random.PCG64(ARRIVAL_SEED))
-        arrivals = np.cumsum(rng.exponential(1.0 / 50.0, size=nq))
-        out.update(db=db, queries=q, arrivals=arrivals)
-        return out
-    raise ValueError(f"unknown workload {k}")
+    db = random_sequences(DB_SEED + 5, n_db or 500_000, 300, 0.65, 20, 1000)
+    nq = n_queries or 10_000
+    q = random_sequences(QUERY_SEED + 5, nq, 400, 0.5, 30, 3000)
+    rng = np.random.Generator(np.random.PCG64(ARRIVAL_SEED))
+    arrivals = np.cumsum(rng.exponential(1.0 / 50.0, size=nq))
+    out.update(db=db, queries=q, arrivals=arrivals)
+    return out
 
 
 def sample_indices(n, k, seed=SAMPLE_SEED):
