@@ -98,7 +98,11 @@ typedef struct sw_options {
                               0 = 16, or 8 for batches too small to fill the GPU */
   int32_t lanes_per_chain; /* lanes per chain of the inter-task kernel, 4..32; 0 = chosen per query */
   int32_t intra_rows;      /* query rows per lane of the intra-task kernel: 8 or 16; 0 = 16 */
-  int32_t reserved[4];     /* must be 0 */
+  int32_t query_pairs;     /* packed mode, inter-task kernel: 0 = pair queries of similar length
+                              into the two 16-bit halves where no lane can overflow (one
+                              database sequence per chain), 1 = never pair (two database
+                              sequences per chain for every query) */
+  int32_t reserved[3];     /* must be 0 */
 } sw_options;
 
 /*

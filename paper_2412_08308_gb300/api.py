@@ -66,9 +66,11 @@ class Database:
             pass
 
 
-def options(cutover=0, rows_per_lane=0, lanes_per_chain=0, intra_rows=0):
-    """Tuning knobs of a query batch (sw_options); 0 keeps the default."""
-    return N.SwOptions(int(cutover), int(rows_per_lane), int(lanes_per_chain), int(intra_rows))
+def options(cutover=0, rows_per_lane=0, lanes_per_chain=0, intra_rows=0, query_pairs=True):
+    """Tuning knobs of a query batch (sw_options); 0 keeps the default.
+    query_pairs=False keeps every packed query in the two-sequences-per-chain form."""
+    return N.SwOptions(int(cutover), int(rows_per_lane), int(lanes_per_chain), int(intra_rows),
+                       0 if query_pairs else 1)
 
 
 class PreparedQueries:

@@ -89,12 +89,14 @@ struct sw_queries {
   int R = 16, Ri = 16;
   Scoring sc{};
   std::vector<QDesc> qd, qdi;  // inter-task and intra-task plans per query
+  std::vector<QDesc> qdp;      // query-pair plans (packed mode, inter-task kernel)
   int64_t n_units = 0, n_long = 0;
   int64_t n_tasks = 0, n_itasks = 0, n_itasks32 = 0, n_rtask_cap = 0;
+  int64_t npairs = 0, n_ptasks = 0, n_solo = 0, n_single = 0;
   bool inter_may_flag = false;  // some packed inter-task pair can exceed the 16-bit threshold
-  int grid = 1, rgrid = 1, igrid = 1, threads = 256;
-  int pbuf_bytes = 0, ipbuf_bytes = 0;
-  size_t smem = 0, ismem = 0;
+  int grid = 1, rgrid = 1, igrid = 1, pgrid = 1, threads = 256;
+  int pbuf_bytes = 0, ipbuf_bytes = 0, ppbuf_bytes = 0;
+  size_t smem = 0, ismem = 0, psmem = 0;
   int32_t gbuf_stride = 0, igbuf_stride = 0;
   int64_t long_stride = 1;
   // device memory (one stream-ordered allocation)
@@ -105,9 +107,9 @@ struct sw_queries {
   cudaEvent_t fork = nullptr, join = nullptr;
   uint8_t *d_qres = nullptr;
   int8_t *d_submat = nullptr;
-  QDesc *d_qd = nullptr, *d_qdi = nullptr;
-  Task *d_tasks = nullptr, *d_itasks = nullptr, *d_itasks32 = nullptr, *d_rtasks = nullptr;
-  int32_t *d_units = nullptr, *d_ipos32 = nullptr;
+  QDesc *d_qd = nullptr, *d_qdi = nullptr, *d_qdp = nullptr;
+  Task *d_tasks = nullptr, *d_itasks = nullptr, *d_itasks32 = nullptr, *d_rtasks = nullptr, *d_ptasks = nullptr;
+  int32_t *d_units = nullptr, *d_ipos32 = nullptr, *d_upos = nullptr;
   uint8_t *d_prof = nullptr;
   int64_t prof_bytes = 0;
   uint2 *d_gbuf = nullptr, *d_igbuf = nullptr;
@@ -120,9 +122,10 @@ struct sw_queries {
   const sw_db *gdb = nullptr;
   int32_t *gscores = nullptr;
   // word layout: [0] inter counter, [1] inter rescue counter, [2] status, [3] inter rescue tasks,
-  // [4] intra (packed) counter, [5] intra (int32) counter, [6], [7] unused,
+  // [4] intra (packed) counter, [5] intra (int32) counter, [6] query-pair counter, [7] unused,
   // [8, 8+nq) inter flag counts, [8+nq, 8+2nq) intra flag counts   -- zeroed every search
-  // [8+2nq] inter tasks, [9+2nq] intra packed tasks, [10+2nq] intra int32 tasks -- constants
+  // [8+2nq] inter tasks, [9+2nq] intra packed tasks, [10+2nq] intra int32 tasks,
+  // [11+2nq] query-pair tasks -- constants
   int64_t zero_words() const { return 8 + 2 * nq; }
 };
 
@@ -131,10 +134,10 @@ namespace {
 // Lanes per chain for one query at R rows per lane: minimise padded rows x
 // pipeline fill x idle lanes, with a small charge per chunk for the
 // boundary strip and the CTA barrier.
-int choose_lanes(int m, int R, double mean_n) {
-  int bestL = 8;
+int choose_lanes(int m, int R, double mean_n, int Lmax = 32) {
+  int bestL = 4;
   double best = 1e300;
-  for (int L = 4; L <= 32; ++L) {
+  for (int L = 4; L <= Lmax; ++L) {
     const int LR = L * R;
     const int C = std::max(1, (m + LR - 1) / LR);
     const double rows = (double)C * LR;
@@ -280,8 +283,9 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
     return fail(SW_EINVAL, "sw_queries_prepare: gap penalties out of range (%d, %d)", gap_open, gap_extend);
   sw_options o{};
   if (opts) o = *opts;
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 3; ++i)
     if (o.reserved[i]) return fail(SW_EINVAL, "sw_queries_prepare: reserved option fields must be 0");
+  if (o.query_pairs != 0 && o.query_pairs != 1) return fail(SW_EINVAL, "sw_queries_prepare: query_pairs must be 0 or 1");
   int R = o.rows_per_lane ? o.rows_per_lane : 16;
   const int Ri = o.intra_rows ? o.intra_rows : 16;
   const int forceL = o.lanes_per_chain;
@@ -356,14 +360,24 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
     }
     return lanes;
   };
-  if (!o.rows_per_lane && lanes_needed(16) < (double)sms * 2048) R = 8;
+  // A small batch is latency-bound: each chain's sweep over its longest
+  // sequence is the critical path, multiplied by the number of chunks.  Use
+  // the fewest chunks the lanes allow (one chunk of up to 32 lanes) rather
+  // than the fewest idle lanes.
+  const bool latency_bound = lanes_needed(16) < (double)sms * 2048;
+  if (!o.rows_per_lane && latency_bound) R = 8;
   Q->R = R;
+  auto pick_lanes = [&](int m, int Lmax) {
+    if (forceL) return std::min(forceL, Lmax);
+    if (latency_bound) return std::min(Lmax, std::max(4, (m + R - 1) / R));
+    return choose_lanes(m, R, mean_n, Lmax);
+  };
   int warps = inter_threads() / 32;
   for (; warps > 2; warps /= 2) {
     int64_t tasks = 0;
     for (int64_t q = 0; q < n_queries; ++q) {
       const int m = std::max<int>(1, (int)(q_offsets[q + 1] - q_offsets[q]));
-      const int chains = warps * (32 / (forceL ? forceL : choose_lanes(m, R, mean_n)));
+      const int chains = warps * (32 / pick_lanes(m, 32));
       tasks += (n_short + chains - 1) / chains;
     }
     if (tasks >= 2 * sms) break;
@@ -371,25 +385,83 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   const int threads = warps * 32;
   Q->threads = threads;
 
-  // --- per-query plans and profile layout
+  // --- query pairs (packed mode).  Two queries of similar length share one
+  // chain: the database residue of a column is common to both, so one 32-bit
+  // profile word per row feeds the two 16-bit halves and the residue-pair
+  // byte shuffle of the two-sequence form disappears.  A pair is formed only
+  // where neither query can pass the 16-bit threshold against the short
+  // database units (the pair form has no rescue pass) and the shorter query
+  // has at least 3/4 of the longer one's rows (the shorter one's padding rows
+  // are wasted work).  The remaining queries keep the two-sequence form.
+  auto qlen = [&](int64_t q) { return (int32_t)(q_offsets[q + 1] - q_offsets[q]); };
+  auto may_flag = [&](int64_t q, int32_t n_upper) {
+    return packed && (int64_t)sc.maxp * std::min<int64_t>(qlen(q), n_upper) > sc.thresh;
+  };
+  const int64_t s0 = packed ? std::min<int64_t>(n, 2 * n_long) : n_long;  // first short sequence
+  Q->n_single = n - s0;
+  std::vector<int32_t> pair_of(n_queries, -1);
+  std::vector<std::pair<int32_t, int32_t>> pairs;
+  if (packed && o.query_pairs == 0 && n_queries >= 2 && Q->n_single > 0) {
+    std::vector<int32_t> ord(n_queries);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) { return qlen(x) > qlen(y); });
+    for (int64_t i = 0; i + 1 < n_queries; ++i) {
+      const int32_t x = ord[i], y = ord[i + 1];
+      if (may_flag(x, max_short) || may_flag(y, max_short)) continue;
+      if (4 * (int64_t)qlen(y) < 3 * (int64_t)qlen(x)) continue;
+      pair_of[x] = (int32_t)pairs.size();
+      pair_of[y] = (int32_t)pairs.size();
+      pairs.emplace_back(x, y);
+      ++i;
+    }
+  }
+  Q->npairs = (int64_t)pairs.size();
+  Q->n_solo = n_queries - 2 * Q->npairs;
+
+  // --- per-query plans and profile layout (queries in a pair get no solo profile)
   Q->qd.resize(n_queries);
   Q->qdi.resize(n_queries);
   int64_t prof = 0;
-  int maxc = 16, maxci = 16;
+  int maxc = 16, maxci = 16, maxcp = 16;
   bool chunked = false, ichunked = false;
   for (int64_t q = 0; q < n_queries; ++q) {
     QDesc &d = Q->qd[q];
-    d.m = (int32_t)(q_offsets[q + 1] - q_offsets[q]);
+    d.m = qlen(q);
     d.R = R;
-    d.L = forceL ? forceL : choose_lanes(std::max(1, d.m), R, mean_n);
+    d.L = pick_lanes(std::max(1, d.m), 32);
     const int LR = d.L * R;
     d.nchunks = std::max(1, (d.m + LR - 1) / LR);
     d.chunk_stride = (int32_t)round_up(LR, 128);
-    d.chunk_bytes = kProfRows * d.chunk_stride;
+    d.chunk_bytes = pair_of[q] < 0 ? kProfRows * d.chunk_stride : 0;
     d.prof_off = prof;
     d.qoff = q_offsets[q];
+    d.qa = d.qb = (int32_t)q;
+    d.ma = d.mb = d.m;
+    d.qoffb = d.qoff;
     prof += (int64_t)d.nchunks * d.chunk_bytes;
     maxc = std::max(maxc, d.chunk_bytes);
+    chunked |= d.chunk_bytes > 0 && d.nchunks > 1;
+  }
+  // pair plans: 4-byte entries; at most 512 rows per chunk keeps two CTAs per SM
+  Q->qdp.resize(Q->npairs);
+  for (int64_t p = 0; p < Q->npairs; ++p) {
+    QDesc &d = Q->qdp[p];
+    d.qa = pairs[p].first;
+    d.qb = pairs[p].second;
+    d.ma = qlen(d.qa);
+    d.mb = qlen(d.qb);
+    d.m = std::max(d.ma, d.mb);
+    d.R = R;
+    d.L = pick_lanes(std::max(1, d.m), std::max(4, std::min(32, 512 / R)));
+    const int LR = d.L * R;
+    d.nchunks = std::max(1, (d.m + LR - 1) / LR);
+    d.chunk_stride = (int32_t)round_up(4 * LR, 128);
+    d.chunk_bytes = kProfRows * d.chunk_stride;
+    d.prof_off = prof;
+    d.qoff = q_offsets[d.qa];
+    d.qoffb = q_offsets[d.qb];
+    prof += (int64_t)d.nchunks * d.chunk_bytes;
+    maxcp = std::max(maxcp, d.chunk_bytes);
     chunked |= d.nchunks > 1;
   }
   if (n_long) {
@@ -397,6 +469,8 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
     for (int64_t q = 0; q < n_queries; ++q) {
       QDesc &d = Q->qdi[q];
       d.m = Q->qd[q].m;
+      d.qa = d.qb = (int32_t)q;
+      d.ma = d.mb = d.m;
       d.R = Ri;
       const int w = (int)std::min<int64_t>(wmax, std::max<int64_t>(1, (d.m + 32 * Ri - 1) / (32 * Ri)));
       d.L = 32 * w;
@@ -406,6 +480,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
       d.chunk_bytes = kProfRows * d.chunk_stride;
       d.prof_off = prof;
       d.qoff = q_offsets[q];
+      d.qoffb = d.qoff;
       prof += (int64_t)d.nchunks * d.chunk_bytes;
       maxci = std::max(maxci, d.chunk_bytes);
       ichunked |= d.nchunks > 1;
@@ -414,21 +489,28 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   Q->prof_bytes = std::max<int64_t>(prof, 16);
   Q->pbuf_bytes = (int)round_up(maxc, 128);
   Q->ipbuf_bytes = (int)round_up(maxci, 128);
+  Q->ppbuf_bytes = (int)round_up(maxcp, 128);
 
   // --- tasks, longest first
   struct TW {
     Task t;
     double w;
   };
-  std::vector<TW> tw, twi, twi32;
+  std::vector<TW> tw, twi, twi32, twp;
   std::vector<int32_t> ipos32;  // database positions of the int32 intra-task units
   int64_t rcap = 0;
-  // a pair scores at most max(SM) * min(m, n): a packed lane that cannot pass the
-  // threshold needs no rescue pass
-  auto may_flag = [&](int64_t q, int32_t n_upper) {
-    return packed && (int64_t)sc.maxp * std::min<int64_t>(Q->qd[q].m, n_upper) > sc.thresh;
-  };
+  // (a pair of sequences scores at most max(SM) * min(m, n): a packed lane
+  // that cannot pass the threshold needs no rescue pass)
+  for (int64_t p = 0; p < Q->npairs; ++p) {  // query pairs x single short sequences
+    const QDesc &d = Q->qdp[p];
+    const int chains = warps * (32 / d.L);
+    for (int64_t i0 = 0; i0 < Q->n_single; i0 += chains) {
+      Task t{(int32_t)p, (int32_t)i0, (int32_t)std::min<int64_t>(chains, Q->n_single - i0), 0};
+      twp.push_back({t, (double)d.nchunks * d.L * d.R * (npad[s0 + i0] + d.L + 8)});
+    }
+  }
   for (int64_t q = 0; q < n_queries && Q->n_units > n_long; ++q) {
+    if (pair_of[q] >= 0) continue;
     const QDesc &d = Q->qd[q];
     const int chains = warps * (32 / d.L);
     for (int64_t u0 = n_long; u0 < Q->n_units; u0 += chains) {
@@ -462,6 +544,8 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   std::stable_sort(tw.begin(), tw.end(), [](const TW &a, const TW &b) { return a.w > b.w; });
   std::stable_sort(twi.begin(), twi.end(), [](const TW &a, const TW &b) { return a.w > b.w; });
   std::stable_sort(twi32.begin(), twi32.end(), [](const TW &a, const TW &b) { return a.w > b.w; });
+  std::stable_sort(twp.begin(), twp.end(), [](const TW &a, const TW &b) { return a.w > b.w; });
+  Q->n_ptasks = (int64_t)twp.size();
   Q->n_tasks = (int64_t)tw.size();
   Q->n_itasks = (int64_t)twi.size();
   Q->n_itasks32 = (int64_t)twi32.size();
@@ -470,14 +554,16 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
 
   // --- launch geometry
   Q->smem = inter_smem_bytes(Q->pbuf_bytes, threads);
+  Q->psmem = inter_smem_bytes(Q->ppbuf_bytes, threads);
   Q->ismem = intra_smem_bytes(Q->ipbuf_bytes);
-  if (Q->smem > 200 * 1024 || (n_long && Q->ismem > 220 * 1024)) {
+  if (Q->smem > 200 * 1024 || Q->psmem > 200 * 1024 || (n_long && Q->ismem > 220 * 1024)) {
     delete Q;
     return fail(SW_EINVAL, "sw_queries_prepare: profile chunk too large for shared memory");
   }
-  const int occ = inter_max_ctas_per_sm(R, packed, threads, Q->smem);
-  const int occ32 = inter_max_ctas_per_sm(R, false, threads, Q->smem);
-  if (occ <= 0 || occ32 <= 0) {
+  const int occ = inter_max_ctas_per_sm(R, packed ? kFormPacked : kFormInt32, threads, Q->smem);
+  const int occ32 = inter_max_ctas_per_sm(R, kFormInt32, threads, Q->smem);
+  const int occp = Q->n_ptasks ? inter_max_ctas_per_sm(R, kFormQPair, threads, Q->psmem) : 1;
+  if (occ <= 0 || occ32 <= 0 || occp <= 0) {
     delete Q;
     return fail(SW_ECUDA, "sw_queries_prepare: cannot configure the inter-task kernel");
   }
@@ -491,8 +577,9 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   }
   Q->grid = (int)std::max<int64_t>(1, std::min<int64_t>(Q->n_tasks, (int64_t)sms * occ));
   Q->rgrid = std::max(1, sms * occ32);
+  Q->pgrid = (int)std::max<int64_t>(1, std::min<int64_t>(Q->n_ptasks, (int64_t)sms * occp));
   Q->igrid = (int)std::max<int64_t>(1, std::min<int64_t>(std::max(Q->n_itasks, Q->n_itasks32), sms));
-  const int gslots = std::max(Q->grid, Q->rgrid);
+  const int gslots = std::max(std::max(Q->grid, Q->rgrid), Q->pgrid);
   Q->gbuf_stride = chunked ? (int32_t)round_up(std::max<int32_t>(16, max_short), 16) : 2;
   Q->igbuf_stride = ichunked ? (int32_t)round_up(std::max<int32_t>(16, max_long), 16) : 2;
 
@@ -506,6 +593,9 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   const size_t b_itasks32 = round_up(sizeof(Task) * std::max<int64_t>(Q->n_itasks32, 1), 256);
   const size_t b_ipos32 = round_up(4 * std::max<int64_t>((int64_t)ipos32.size(), 1), 256);
   const size_t b_rtasks = round_up(sizeof(Task) * std::max<int64_t>(Q->n_rtask_cap, 1), 256);
+  const size_t b_qdp = round_up(sizeof(QDesc) * std::max<int64_t>(Q->npairs, 1), 256);
+  const size_t b_ptasks = round_up(sizeof(Task) * std::max<int64_t>(Q->n_ptasks, 1), 256);
+  const size_t b_upos = round_up(4 * std::max<int64_t>(Q->npairs ? Q->n_single : 0, 1), 256);
   const size_t b_units = round_up(4 * (int64_t)units.size(), 256);
   const size_t b_prof = round_up(Q->prof_bytes, 256);
   const size_t b_gbuf = round_up((int64_t)gslots * warps * 8 * (int64_t)Q->gbuf_stride * 8, 256);
@@ -514,7 +604,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   const size_t b_flag = Q->inter_may_flag ? round_up(4 * nqm * std::max<int64_t>(n, 1), 256) : 0;
   const size_t b_iflag = packed ? round_up(4 * nqm * Q->long_stride, 256) : 0;
   Q->bytes = b_qres + b_sub + 2 * b_qd + b_tasks + b_itasks + b_itasks32 + b_ipos32 + b_rtasks + b_units + b_prof +
-             b_gbuf + b_igbuf + b_words + b_flag + b_iflag;
+             b_gbuf + b_igbuf + b_words + b_flag + b_iflag + b_qdp + b_ptasks + b_upos;
   cudaError_t e = cudaMallocAsync(&Q->block, Q->bytes, s);
   if (e != cudaSuccess) {
     delete Q;
@@ -542,15 +632,23 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   Q->d_words = (int32_t *)take(b_words);
   Q->d_flag_pos = Q->inter_may_flag ? (int32_t *)take(b_flag) : nullptr;
   Q->d_iflag_pos = packed ? (int32_t *)take(b_iflag) : nullptr;
+  Q->d_qdp = (QDesc *)take(b_qdp);
+  Q->d_ptasks = (Task *)take(b_ptasks);
+  Q->d_upos = (int32_t *)take(b_upos);
 
-  std::vector<Task> tasks(Q->n_tasks), itasks(Q->n_itasks), itasks32(Q->n_itasks32);
+  std::vector<Task> tasks(Q->n_tasks), itasks(Q->n_itasks), itasks32(Q->n_itasks32), ptasks(Q->n_ptasks);
+  std::vector<int32_t> upos(Q->npairs ? Q->n_single : 0);
+  for (int64_t i = 0; i < (int64_t)upos.size(); ++i) upos[i] = (int32_t)(s0 + i);
+  for (int64_t i = 0; i < Q->n_ptasks; ++i) ptasks[i] = twp[i].t;
   for (int64_t i = 0; i < Q->n_tasks; ++i) tasks[i] = tw[i].t;
   for (int64_t i = 0; i < Q->n_itasks; ++i) itasks[i] = twi[i].t;
   for (int64_t i = 0; i < Q->n_itasks32; ++i) itasks32[i] = twi32[i].t;
-  const int32_t consts[3] = {(int32_t)Q->n_tasks, (int32_t)Q->n_itasks, (int32_t)Q->n_itasks32};
+  const int32_t consts[4] = {(int32_t)Q->n_tasks, (int32_t)Q->n_itasks, (int32_t)Q->n_itasks32,
+                             (int32_t)Q->n_ptasks};
   Q->h2d_bytes = q_offsets[n_queries] + 400 + 2 * (int64_t)sizeof(QDesc) * n_queries +
-                 (int64_t)sizeof(Task) * (Q->n_tasks + Q->n_itasks + Q->n_itasks32) + 4 * (int64_t)units.size() +
-                 4 * (int64_t)ipos32.size() + 12;
+                 (int64_t)sizeof(QDesc) * Q->npairs +
+                 (int64_t)sizeof(Task) * (Q->n_tasks + Q->n_itasks + Q->n_itasks32 + Q->n_ptasks) +
+                 4 * (int64_t)units.size() + 4 * (int64_t)ipos32.size() + 4 * (int64_t)upos.size() + 16;
   e = cudaSuccess;
   if (q_offsets[n_queries] > 0)
     e = cudaMemcpyAsync(Q->d_qres, queries, q_offsets[n_queries], cudaMemcpyHostToDevice, s);
@@ -567,6 +665,13 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
     e = cudaMemcpyAsync(Q->d_itasks32, itasks32.data(), sizeof(Task) * Q->n_itasks32, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(Q->d_ipos32, ipos32.data(), 4 * ipos32.size(), cudaMemcpyHostToDevice, s);
+  }
+  if (e == cudaSuccess && Q->npairs) {
+    e = cudaMemcpyAsync(Q->d_qdp, Q->qdp.data(), sizeof(QDesc) * Q->npairs, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && Q->n_ptasks)
+      e = cudaMemcpyAsync(Q->d_ptasks, ptasks.data(), sizeof(Task) * Q->n_ptasks, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !upos.empty())
+      e = cudaMemcpyAsync(Q->d_upos, upos.data(), 4 * upos.size(), cudaMemcpyHostToDevice, s);
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(Q->d_units, units.data(), 4 * units.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(Q->d_words, 0, b_words, s);
@@ -605,7 +710,11 @@ int sw_search_prepared(const sw_db *db, const sw_queries *Q, int32_t *scores_dev
   int32_t *w = Q->d_words;
 
   SW_CUDA(cudaMemsetAsync(w, 0, 4 * Q->zero_words(), s), "memset");
-  SW_CUDA(launch_build_profiles(Q->d_qres, Q->d_qd, nq, Q->d_submat, Q->sc.pad, Q->d_prof, s), "profile kernel");
+  if (Q->n_solo)
+    SW_CUDA(launch_build_profiles(Q->d_qres, Q->d_qd, nq, Q->d_submat, Q->sc.pad, Q->d_prof, s), "profile kernel");
+  if (Q->npairs)
+    SW_CUDA(launch_build_pair_profiles(Q->d_qres, Q->d_qdp, (int32_t)Q->npairs, Q->d_submat, Q->sc.pad, Q->d_prof, s),
+            "pair profile kernel");
   if (Q->n_long)
     SW_CUDA(launch_build_profiles(Q->d_qres, Q->d_qdi, nq, Q->d_submat, Q->sc.pad, Q->d_prof, s),
             "profile kernel");
@@ -647,6 +756,22 @@ int sw_search_prepared(const sw_db *db, const sw_queries *Q, int32_t *scores_dev
     SW_CUDA(cudaEventRecord(Q->join, Q->side), "event");
   }
 
+  if (Q->timing && (Q->n_tasks || Q->n_ptasks)) SW_CUDA(cudaEventRecord(Q->ev0, s), "event");
+  if (Q->n_ptasks) {  // query pairs, one short database sequence per chain
+    InterArgs p = a;
+    p.qd = Q->d_qdp;
+    p.unit_pos = Q->d_upos;
+    p.tasks = Q->d_ptasks;
+    p.n_tasks = w + Q->zero_words() + 3;
+    p.task_counter = w + 6;
+    p.pbuf_bytes = Q->ppbuf_bytes;
+    p.gbuf = Q->d_gbuf;
+    p.gbuf_stride = Q->gbuf_stride;
+    p.flag_count = nullptr;
+    p.flag_pos = nullptr;
+    p.flag_stride = 0;
+    SW_CUDA(launch_inter(p, Q->R, kFormQPair, Q->pgrid, threads, Q->psmem, s), "inter-task kernel (query pairs)");
+  }
   if (Q->n_tasks) {
     a.qd = Q->d_qd;
     a.tasks = Q->d_tasks;
@@ -658,12 +783,13 @@ int sw_search_prepared(const sw_db *db, const sw_queries *Q, int32_t *scores_dev
     a.flag_count = w + 8;
     a.flag_pos = Q->d_flag_pos;
     a.flag_stride = db->n;
-    if (Q->timing) SW_CUDA(cudaEventRecord(Q->ev0, s), "event");
-    SW_CUDA(launch_inter(a, Q->R, packed, Q->grid, threads, Q->smem, s), "inter-task kernel");
-    if (Q->timing) {
-      SW_CUDA(cudaEventRecord(Q->ev1, s), "event");
-      const_cast<sw_queries *>(Q)->timed = true;
-    }
+    SW_CUDA(launch_inter(a, Q->R, packed ? kFormPacked : kFormInt32, Q->grid, threads, Q->smem, s), "inter-task kernel");
+  }
+  if (Q->timing && (Q->n_tasks || Q->n_ptasks)) {
+    SW_CUDA(cudaEventRecord(Q->ev1, s), "event");
+    const_cast<sw_queries *>(Q)->timed = true;
+  }
+  if (Q->n_tasks) {
     if (Q->inter_may_flag) {
       SW_CUDA(launch_rescue_tasks(w + 8, Q->d_qd, nq, db->n, threads / 32, 0, Q->d_rtasks, w + 3, w + 1, s),
               "rescue task kernel");
@@ -674,7 +800,7 @@ int sw_search_prepared(const sw_db *db, const sw_queries *Q, int32_t *scores_dev
       r.task_counter = w + 1;
       r.flag_count = nullptr;
       r.flag_pos = nullptr;
-      SW_CUDA(launch_inter(r, Q->R, false, Q->rgrid, threads, Q->smem, s), "inter-task rescue kernel");
+      SW_CUDA(launch_inter(r, Q->R, kFormInt32, Q->rgrid, threads, Q->smem, s), "inter-task rescue kernel");
     }
   }
   if (Q->n_long) SW_CUDA(cudaStreamWaitEvent(s, Q->join, 0), "event");
@@ -731,6 +857,7 @@ int sw_queries_status(const sw_queries *Q, void *stream, int64_t *rescued) {
   }
   if (rescued) *rescued = inter_flags;
   if (w[2] == SW_ETIMEOUT) return fail(SW_ETIMEOUT, "a bounded device wait expired");
+  if (w[2] == kStatusSaturated) return fail(SW_ECUDA, "internal error: a query-pair lane passed its bound");
   if (intra_flags) return fail(SW_ECUDA, "internal error: a packed intra-task lane passed its bound");
   return SW_OK;
 }
@@ -763,8 +890,8 @@ int sw_queries_info(const sw_queries *q, int64_t *h2d_bytes, int64_t *device_byt
   if (launches) {
     int64_t k = 0;
     if (q->nq > 0 && q->db->n > 0) {
-      k = 1 + (q->n_long ? 1 : 0);                       // profile builds
-      k += q->n_tasks ? 1 : 0;                            // inter-task kernel
+      k = (q->n_solo ? 1 : 0) + (q->npairs ? 1 : 0) + (q->n_long ? 1 : 0);  // profile builds
+      k += (q->n_tasks ? 1 : 0) + (q->n_ptasks ? 1 : 0);  // inter-task kernels
       k += (q->n_tasks && q->inter_may_flag) ? 2 : 0;     // rescue tasks + int32 rescue
       k += (q->n_itasks ? 1 : 0) + (q->n_itasks32 ? 1 : 0);
     }
@@ -772,7 +899,7 @@ int sw_queries_info(const sw_queries *q, int64_t *h2d_bytes, int64_t *device_byt
   }
   if (h2d_bytes) *h2d_bytes = q->h2d_bytes;
   if (device_bytes) *device_bytes = (int64_t)q->bytes;
-  if (n_tasks) *n_tasks = q->n_tasks + q->n_itasks + q->n_itasks32;
+  if (n_tasks) *n_tasks = q->n_tasks + q->n_itasks + q->n_itasks32 + q->n_ptasks;
   return SW_OK;
 }
 

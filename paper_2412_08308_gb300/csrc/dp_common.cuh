@@ -87,20 +87,21 @@ __device__ __forceinline__ uint32_t word_of(const uint4 &v, int i) {
   return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
 }
 
-template <bool PACKED>
-using Word = typename std::conditional<PACKED, uint32_t, int32_t>::type;
+template <int FORM>
+using Word = typename std::conditional<FORM != kFormInt32, uint32_t, int32_t>::type;
 
 // Per-lane DP state of R rows.
-template <int R, bool PACKED>
+template <int R, int FORM>
 struct LaneState {
-  Word<PACKED> Hl[R];  // H of each row at the previous column
-  Word<PACKED> E[R];   // packed: E of each row at the current column; int32: E at the previous column
-  Word<PACKED> hdiag;  // H of the row above this lane's first row, previous column
+  Word<FORM> Hl[R];  // H of each row at the previous column
+  Word<FORM> E[R];   // packed: E of each row at the current column; int32: E at the previous column
+  Word<FORM> hdiag;  // H of the row above this lane's first row, previous column
 };
 
-template <int R, bool PACKED>
-__device__ __forceinline__ void lane_reset(LaneState<R, PACKED> &st, const Consts &cs) {
-  using W = Word<PACKED>;
+template <int R, int FORM>
+__device__ __forceinline__ void lane_reset(LaneState<R, FORM> &st, const Consts &cs) {
+  using W = Word<FORM>;
+  constexpr bool PACKED = FORM != kFormInt32;
   const W E0 = PACKED ? (W)cs.E0W : (W)0;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
@@ -112,14 +113,45 @@ __device__ __forceinline__ void lane_reset(LaneState<R, PACKED> &st, const Const
 
 // One column: inputs are the (H, F) pair passed down from the row above this
 // lane's rows and the residue code(s) of the column; prow points at this
-// lane's R profile bytes of residue row 0 (rows are `stride` bytes apart).
+// lane's R profile entries of residue row 0 (rows are `stride` bytes apart).
+// Query-pair form: prow points at this lane's first 16-byte group of four
+// words; its R/4 groups are `gstride` bytes apart (lanes interleaved, so the
+// 32 lanes of a warp read 32 consecutive 16-byte groups: no bank conflict).
 // Outputs the (H, F) pair for the row below: int32 passes (H, F) of the last
 // row; packed passes (H of the last row, F of the row below it).
-template <int R, bool PACKED>
-__device__ __forceinline__ void column_step(LaneState<R, PACKED> &st, const uint8_t *prow, int stride,
-                                            uint32_t res, Word<PACKED> inH, Word<PACKED> inF, const Consts &cs,
-                                            Word<PACKED> &S, Word<PACKED> &outH, Word<PACKED> &outF) {
-  using W = Word<PACKED>;
+template <int R, int FORM>
+__device__ __forceinline__ void column_step(LaneState<R, FORM> &st, const uint8_t *prow, int stride,
+                                            uint32_t res, Word<FORM> inH, Word<FORM> inF, const Consts &cs,
+                                            Word<FORM> &S, Word<FORM> &outH, Word<FORM> &outF, int gstride = 0) {
+  using W = Word<FORM>;
+  if constexpr (FORM == kFormQPair) {
+    // the two queries' scores for this column's residue, one word per row
+    uint32_t pw[R];
+#pragma unroll
+    for (int i = 0; i < R / 4; ++i) {
+      const uint4 v = *reinterpret_cast<const uint4 *>(prow + (res & 0xffu) * stride + i * gstride);
+      pw[4 * i + 0] = v.x; pw[4 * i + 1] = v.y; pw[4 * i + 2] = v.z; pw[4 * i + 3] = v.w;
+    }
+    uint32_t hd = (uint32_t)st.hdiag, f = (uint32_t)inF, s = (uint32_t)S;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const uint32_t x = __vadd2(hd, pw[r]);
+      const uint32_t tt = __vimax_s16x2_relu(x, (uint32_t)st.E[r]);
+      const uint32_t h = __vmaxs2(tt, f);
+      s = __vmaxs2(s, h);
+      const uint32_t hgo = __vsub2(h, cs.goW);
+      st.E[r] = (W)__vmaxs2(__vsub2((uint32_t)st.E[r], cs.geW), hgo);
+      f = __vmaxs2(__vsub2(f, cs.geW), hgo);
+      hd = (uint32_t)st.Hl[r];
+      st.Hl[r] = (W)h;
+    }
+    S = (W)s;
+    outH = st.Hl[R - 1];
+    outF = (W)f;
+    st.hdiag = inH;
+    return;
+  }
+  constexpr bool PACKED = FORM == kFormPacked;
   uint32_t pa[R / 4];
   load_prof<R>(prow + (res & 0xffu) * stride, pa);
   if constexpr (PACKED) {
@@ -170,16 +202,27 @@ __device__ __forceinline__ void column_step(LaneState<R, PACKED> &st, const uint
   st.hdiag = inH;
 }
 
-template <bool PACKED>
-__device__ __forceinline__ Word<PACKED> score_max(Word<PACKED> a, Word<PACKED> b) {
-  if constexpr (PACKED) return (Word<PACKED>)__vmaxs2((uint32_t)a, (uint32_t)b);
+template <int FORM>
+__device__ __forceinline__ Word<FORM> score_max(Word<FORM> a, Word<FORM> b) {
+  if constexpr (FORM != kFormInt32) return (Word<FORM>)__vmaxs2((uint32_t)a, (uint32_t)b);
   else return max(a, b);
 }
 
-// Epilogue for one database unit: un-bias, flag possible overflows (packed)
-// and scatter to caller order.
-template <bool PACKED>
-__device__ __forceinline__ void write_scores(Word<PACKED> S, int posA, int posB, int q, const InterArgs &a) {
+// Epilogue for one database unit: flag possible overflows (packed) and scatter
+// to caller order.  Query-pair units write the two halves to their queries;
+// they are planned only where no lane can pass the threshold.
+template <int FORM>
+__device__ __forceinline__ void write_scores(Word<FORM> S, int posA, int posB, int q, const QDesc &qd,
+                                             const InterArgs &a) {
+  constexpr bool PACKED = FORM == kFormPacked;
+  if constexpr (FORM == kFormQPair) {
+    const int32_t sa = (int32_t)((uint32_t)S & 0xffffu), sb = (int32_t)((uint32_t)S >> 16);
+    if (sa > a.sc.thresh || sb > a.sc.thresh) atomicExch(a.status, kStatusSaturated);
+    const int32_t p = a.db.perm[posA];
+    a.out[(int64_t)qd.qa * a.out_stride + p] = sa;
+    if (qd.qb != qd.qa) a.out[(int64_t)qd.qb * a.out_stride + p] = sb;
+    return;
+  }
   const DbView &db = a.db;
   const Scoring &sc = a.sc;
   int32_t *out = a.out;

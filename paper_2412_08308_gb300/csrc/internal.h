@@ -27,15 +27,25 @@ struct Scoring {
 
 // Per-query descriptor for the dynamic-programming kernels.
 struct QDesc {
-  int32_t m;         // query length
+  int32_t m;         // query length (query-pair plans: the longer of the two)
   int32_t L;         // lanes per chain (1..32)
   int32_t R;         // rows per lane
   int32_t nchunks;   // ceil(m / (L*R)) (>= 1)
   int32_t chunk_bytes;  // bytes of one profile chunk = 21 * chunk_stride
-  int32_t chunk_stride; // bytes per profile row within a chunk (>= L*R, multiple of 16)
+  int32_t chunk_stride; // bytes per profile row within a chunk (>= L*R entries, multiple of 128)
   int64_t prof_off;  // byte offset of chunk 0 in the profile buffer
   int64_t qoff;      // offset of the query residues in the query residue buffer
+  // query-pair plans (two queries in the two 16-bit halves; single-query
+  // plans repeat the query): query indices, lengths and residue offsets
+  int32_t qa, qb, ma, mb;
+  int64_t qoffb;
 };
+
+// Forms of the dynamic-programming kernels.
+constexpr int kFormInt32 = 0;   // one database sequence per chain, 32-bit cells
+constexpr int kFormPacked = 1;  // two database sequences per chain, 16-bit halves
+constexpr int kFormQPair = 2;   // two queries per chain (one sequence), 16-bit halves
+constexpr int32_t kStatusSaturated = 100;  // device status: a lane that could not saturate did
 
 // A unit of DP work for one chain: one database sequence (int32 form) or
 // two (packed form), given as positions in the length-sorted database.
@@ -80,11 +90,11 @@ int inter_threads();
 int inter_chains_per_cta(int L);
 bool inter_supported_R(int R);
 size_t inter_smem_bytes(int pbuf_bytes, int threads);
-cudaError_t launch_inter(const InterArgs &a, int R, bool packed, int grid, int threads, size_t smem,
+cudaError_t launch_inter(const InterArgs &a, int R, int form, int grid, int threads, size_t smem,
                          cudaStream_t s);
 // Raises the instantiation's shared-memory limit (plan time only) and returns resident CTAs per SM
 // (0 on failure).
-int inter_max_ctas_per_sm(int R, bool packed, int threads, size_t smem);
+int inter_max_ctas_per_sm(int R, int form, int threads, size_t smem);
 
 // intra-task kernel (k_intra.cu): one CTA of intra_threads() per (query, unit) task;
 // QDesc::L = 32 * warps of the chain.
@@ -96,6 +106,10 @@ cudaError_t launch_intra(const InterArgs &a, int R, bool packed, int grid, size_
 // support kernels (k_support.cu)
 cudaError_t launch_build_profiles(const uint8_t *qres, const QDesc *qd, int32_t nq, const int8_t *submat,
                                   int32_t pad, uint8_t *prof, cudaStream_t s);
+// Query-pair tables: per chunk [21][chunk_stride] bytes of 32-bit words
+// (SM(Qa[i], c) & 0xffff) | (SM(Qb[i], c) << 16).
+cudaError_t launch_build_pair_profiles(const uint8_t *qres, const QDesc *qd, int32_t npairs, const int8_t *submat,
+                                       int32_t pad, uint8_t *prof, cudaStream_t s);
 // Build rescue tasks from the per-query flag counts: tiles of warps_per_cta * (32 / L) flagged
 // positions (units_per_task == 0) or of units_per_task positions; flagged positions of query q
 // start at q * stride.  Writes the task count to *n_tasks and zeroes *counter.

@@ -44,17 +44,19 @@ constexpr int kChainsPerWarpMax = 8;  // lanes per chain >= 4
 constexpr int kRingBytes = 320;       // residues: 2 slots x 2 seqs x 16 B; boundary: 2 slots x 16 x 8 B
 
 // One pass of a chain over all columns of its unit for the rows of one chunk.
-template <int R, bool PACKED>
+template <int R, int FORM>
 __device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, const int stride, const int L,
                                            const int k, const int lane, const bool live, const int nblk,
                                            const int npad, const int npa, const int npb,
                                            const uint8_t *__restrict__ resA, const uint8_t *__restrict__ resB,
                                            uint8_t *ring, uint2 *gb, const bool prev, const bool next,
-                                           const Consts &cs, Word<PACKED> &S) {
-  using W = Word<PACKED>;
+                                           const Consts &cs, Word<FORM> &S) {
+  using W = Word<FORM>;
+  constexpr bool PACKED = FORM != kFormInt32;      // 16-bit halves
+  constexpr bool PAIRS = FORM == kFormPacked;      // two database sequences per unit
   const W H0 = (W)0;
   const W F0 = PACKED ? (W)cs.F0W : (W)0;
-  LaneState<R, PACKED> st;
+  LaneState<R, FORM> st;
   lane_reset(st, cs);
   W outH = H0, outF = F0;
   uint32_t outRes = kPadPair;
@@ -63,7 +65,9 @@ __device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, cons
   const bool tail = live && (k == L - 1) && next;
   uint8_t *rres = ring;                                  // [slot][seq][16 B]
   uint2 *rgb = reinterpret_cast<uint2 *>(ring + 64);     // [slot][16]
-  const uint8_t *prow = pch + k * R;
+  // query pairs: lane k's word groups sit at k*16 + i*L*16 (lanes interleaved)
+  const uint8_t *prow = FORM == kFormQPair ? pch + k * 16 : pch + k * R;
+  const int gstride = L * 16;
 
   auto prefetch = [&](int blk) {
     const int slot = blk & 1;
@@ -71,7 +75,7 @@ __device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, cons
     uint8_t *d = rres + slot * 32;
     if (col < npa) cp_async16(d, resA + col);
     else *reinterpret_cast<uint4 *>(d) = make_uint4(0x14141414u, 0x14141414u, 0x14141414u, 0x14141414u);
-    if (PACKED) {
+    if (PAIRS) {
       if (col < npb) cp_async16(d + 16, resB + col);
       else *reinterpret_cast<uint4 *>(d + 16) = make_uint4(0x14141414u, 0x14141414u, 0x14141414u, 0x14141414u);
     }
@@ -91,7 +95,7 @@ __device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, cons
     if (lead) {
       cp_async_wait<1>();
       ra4 = *reinterpret_cast<const uint4 *>(rres + (blk & 1) * 32);
-      if (PACKED) rb4 = *reinterpret_cast<const uint4 *>(rres + (blk & 1) * 32 + 16);
+      if (PAIRS) rb4 = *reinterpret_cast<const uint4 *>(rres + (blk & 1) * 32 + 16);
     }
     const uint2 *gslot = rgb + (blk & 1) * 16;
     // lane 0's columns of this block are all real or all padding (npad is a multiple of 16)
@@ -110,7 +114,7 @@ __device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, cons
         W inF = (W)__shfl_sync(0xffffffffu, outF, src);
         uint32_t inRes = __shfl_sync(0xffffffffu, outRes, src);
         if (k == 0) {
-          const uint32_t rr = PACKED ? prmt(wa, wb, sel_pair(s4)) : prmt(wa, 0u, sel_one(s4));
+          const uint32_t rr = PAIRS ? prmt(wa, wb, sel_pair(s4)) : prmt(wa, 0u, sel_one(s4));
           inRes = real ? rr : kPadPair;
           if (from_strip) {
             const uint2 v = gslot[s];
@@ -121,7 +125,7 @@ __device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, cons
             inF = F0;
           }
         }
-        column_step<R, PACKED>(st, prow, stride, inRes, inH, inF, cs, S, outH, outF);
+        column_step<R, FORM>(st, prow, stride, inRes, inH, inF, cs, S, outH, outF, gstride);
         outRes = inRes;
         if (tail) {
           const int j = t - (L - 1);
@@ -137,9 +141,10 @@ __device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, cons
   if (lead) cp_async_wait<0>();
 }
 
-template <int R, bool PACKED>
+template <int R, int FORM>
 __global__ void __launch_bounds__(kThreads, 2) inter_kernel(const InterArgs a) {
-  using W = Word<PACKED>;
+  using W = Word<FORM>;
+  constexpr bool PAIRS = FORM == kFormPacked;
   extern __shared__ __align__(128) uint8_t smem[];
   uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
   volatile int *s_task = reinterpret_cast<volatile int *>(smem + 16);
@@ -176,10 +181,10 @@ __global__ void __launch_bounds__(kThreads, 2) inter_kernel(const InterArgs a) {
     int posA = 0, posB = 0, npa = 0, npb = 0;
     if (live) {
       const int u = tk.unit_begin + ci;
-      posA = a.unit_pos[PACKED ? 2 * u : u];
-      posB = PACKED ? a.unit_pos[2 * u + 1] : posA;
+      posA = a.unit_pos[PAIRS ? 2 * u : u];
+      posB = PAIRS ? a.unit_pos[2 * u + 1] : posA;
       npa = a.db.npad[posA];
-      npb = PACKED ? a.db.npad[posB] : 0;
+      npb = PAIRS ? a.db.npad[posB] : 0;
     }
     const int npad = max(npa, npb);
     const int nblk = __reduce_max_sync(0xffffffffu, live ? (npad + L - 1 + kColBlock - 1) / kColBlock : 0);
@@ -210,31 +215,31 @@ __global__ void __launch_bounds__(kThreads, 2) inter_kernel(const InterArgs a) {
         if (threadIdx.x == 0) atomicExch(a.status, SW_ETIMEOUT);
         return;
       }
-      chain_pass<R, PACKED>(pbuf + b * a.pbuf_bytes, qd.chunk_stride, L, k, lane, live, nblk, npad, npa, npb,
+      chain_pass<R, FORM>(pbuf + b * a.pbuf_bytes, qd.chunk_stride, L, k, lane, live, nblk, npad, npa, npb,
                             resA, resB, ring, gb, c > 0, c + 1 < qd.nchunks, cs, S);
       __syncthreads();
       if (threadIdx.x == 0 && c + 2 < qd.nchunks) issue(c + 2);
     }
 
     // max over the chain's lanes
-    for (int d = 1; d < L; d <<= 1) S = score_max<PACKED>(S, (W)__shfl_sync(0xffffffffu, S, (k + d < L) ? lane + d : lane));
+    for (int d = 1; d < L; d <<= 1) S = score_max<FORM>(S, (W)__shfl_sync(0xffffffffu, S, (k + d < L) ? lane + d : lane));
     if (live && k == 0)
-      write_scores<PACKED>(S, posA, posB, tk.q, a);
+      write_scores<FORM>(S, posA, posB, tk.q, qd, a);
   }
 }
 
-template <int R, bool PACKED>
+template <int R, int FORM>
 cudaError_t launch_one(const InterArgs &a, int grid, int threads, size_t smem, cudaStream_t s) {
-  inter_kernel<R, PACKED><<<grid, threads, smem, s>>>(a);
+  inter_kernel<R, FORM><<<grid, threads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 // Raise the dynamic shared-memory limit of an instantiation (done at plan time,
 // never inside a launch sequence that may be captured into a graph) and return
 // its resident CTAs per SM for the given block size and shared memory.
-template <int R, bool PACKED>
+template <int R, int FORM>
 int configure_one(int threads, size_t smem) {
-  auto kern = inter_kernel<R, PACKED>;
+  auto kern = inter_kernel<R, FORM>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -267,22 +272,29 @@ bool inter_supported_R(int R) {
   return false;
 }
 
-cudaError_t launch_inter(const InterArgs &a, int R, bool packed, int grid, int threads, size_t smem,
+cudaError_t launch_inter(const InterArgs &a, int R, int form, int grid, int threads, size_t smem,
                          cudaStream_t s) {
-#define SWGB_CASE(RR)                                                        \
-  if (R == RR) return packed ? launch_one<RR, true>(a, grid, threads, smem, s) \
-                             : launch_one<RR, false>(a, grid, threads, smem, s);
+#define SWGB_CASE(RR)                                                                   \
+  if (R == RR) {                                                                        \
+    if (form == kFormInt32) return launch_one<RR, kFormInt32>(a, grid, threads, smem, s);   \
+    if (form == kFormPacked) return launch_one<RR, kFormPacked>(a, grid, threads, smem, s); \
+    if (form == kFormQPair) return launch_one<RR, kFormQPair>(a, grid, threads, smem, s);   \
+  }
   SWGB_INTER_R_LIST(SWGB_CASE)
 #undef SWGB_CASE
   return cudaErrorInvalidValue;
 }
 
-int inter_max_ctas_per_sm(int R, bool packed, int threads, size_t smem) {
-#define SWGB_CASE(RR) \
-  if (R == RR) return packed ? configure_one<RR, true>(threads, smem) : configure_one<RR, false>(threads, smem);
+int inter_max_ctas_per_sm(int R, int form, int threads, size_t smem) {
+#define SWGB_CASE(RR)                                                                \
+  if (R == RR) {                                                                     \
+    if (form == kFormInt32) return configure_one<RR, kFormInt32>(threads, smem);     \
+    if (form == kFormPacked) return configure_one<RR, kFormPacked>(threads, smem);   \
+    if (form == kFormQPair) return configure_one<RR, kFormQPair>(threads, smem);     \
+  }
   SWGB_INTER_R_LIST(SWGB_CASE)
 #undef SWGB_CASE
-  return 1;
+  return 0;
 }
 
 }  // namespace swgb

@@ -48,7 +48,8 @@ __device__ __forceinline__ bool wait_at_least(volatile int32_t *p, int32_t v, vo
 
 template <int R, bool PACKED>
 __global__ void __launch_bounds__(kIntraThreads, 1) intra_kernel(const InterArgs a) {
-  using W = Word<PACKED>;
+  constexpr int FORM = PACKED ? kFormPacked : kFormInt32;
+  using W = Word<FORM>;
   extern __shared__ __align__(128) uint8_t smem[];
   IntraShared *sh = reinterpret_cast<IntraShared *>(smem);
   uint8_t *pbuf = smem + 256;
@@ -114,7 +115,7 @@ __global__ void __launch_bounds__(kIntraThreads, 1) intra_kernel(const InterArgs
       }
 
       if (wlive) {
-        LaneState<R, PACKED> st;
+        LaneState<R, FORM> st;
         lane_reset(st, cs);
         W outH = H0, outF = F0;
         uint32_t outRes = kPadPair;
@@ -188,7 +189,7 @@ __global__ void __launch_bounds__(kIntraThreads, 1) intra_kernel(const InterArgs
                   inRes = v.z;
                 }
               }
-              column_step<R, PACKED>(st, prow, qd.chunk_stride, inRes, inH, inF, cs, S, outH, outF);
+              column_step<R, FORM>(st, prow, qd.chunk_stride, inRes, inH, inF, cs, S, outH, outF);
               outRes = inRes;
               if (lane == 31) {
                 const int col = tau - 31;
@@ -213,13 +214,13 @@ __global__ void __launch_bounds__(kIntraThreads, 1) intra_kernel(const InterArgs
     }
 
     // max over the whole chain
-    for (int d = 16; d > 0; d >>= 1) S = score_max<PACKED>(S, (W)__shfl_xor_sync(0xffffffffu, S, d));
+    for (int d = 16; d > 0; d >>= 1) S = score_max<FORM>(S, (W)__shfl_xor_sync(0xffffffffu, S, d));
     if (lane == 0) sh->smax[warp] = (uint32_t)S;
     __syncthreads();
     if (threadIdx.x == 0) {
       W m = (W)sh->smax[0];
-      for (int w = 1; w < Wq; ++w) m = score_max<PACKED>(m, (W)sh->smax[w]);
-      write_scores<PACKED>(m, posA, posB, tk.q, a);
+      for (int w = 1; w < Wq; ++w) m = score_max<FORM>(m, (W)sh->smax[w]);
+      write_scores<FORM>(m, posA, posB, tk.q, qd, a);
     }
     __syncthreads();
   }

@@ -40,6 +40,44 @@ __global__ void build_profiles_kernel(const uint8_t *__restrict__ qres, const QD
   }
 }
 
+// Query-pair profile: the same table for two queries qa and qb, one 32-bit
+// entry per (residue, row) holding SM(Qa[i], c) in the low and SM(Qb[i], c) in
+// the high 16-bit half (both sign-extended).  Rows past a query's own end,
+// the pad residue and entries past L*R hold `pad`.  Layout per pair: nchunks
+// chunks of [21][chunk_stride] bytes.  Within a residue row the lanes'
+// four-word groups are interleaved: row x = k*R + 4*i + j of the chunk (lane
+// k, group i, word j) sits at word (i*L + k)*4 + j, so the lanes of a warp
+// read consecutive 16-byte groups.
+__global__ void build_pair_profiles_kernel(const uint8_t *__restrict__ qres, const QDesc *__restrict__ qd,
+                                           const int8_t *__restrict__ submat, int32_t pad,
+                                           uint8_t *__restrict__ prof) {
+  __shared__ int8_t sm[kAlphabet * kAlphabet];
+  for (int i = threadIdx.x; i < kAlphabet * kAlphabet; i += blockDim.x) sm[i] = submat[i];
+  __syncthreads();
+  const QDesc d = qd[blockIdx.y];
+  const uint8_t *qa = qres + d.qoff;
+  const uint8_t *qb = qres + d.qoffb;
+  const int LR = d.L * d.R;
+  const int64_t words = (int64_t)d.nchunks * d.chunk_bytes / 4;
+  uint32_t *out = reinterpret_cast<uint32_t *>(prof + d.prof_off);
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words; w += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t x0 = 4 * w;
+    const int c = (int)(x0 / d.chunk_bytes);
+    const int rem = (int)(x0 - (int64_t)c * d.chunk_bytes);
+    const int rho = rem / d.chunk_stride;
+    const int wi = (rem - rho * d.chunk_stride) / 4;
+    const int gi = wi / (4 * d.L), kk = (wi >> 2) - gi * d.L;
+    const int xx = kk * d.R + 4 * gi + (wi & 3);
+    const int row = c * LR + xx;
+    int32_t va = pad, vb = pad;
+    if (wi < LR && rho < kAlphabet) {
+      if (row < d.ma) va = sm[qa[row] * kAlphabet + rho];
+      if (row < d.mb) vb = sm[qb[row] * kAlphabet + rho];
+    }
+    out[w] = ((uint32_t)va & 0xffffu) | ((uint32_t)vb << 16);
+  }
+}
+
 // One task per tile of up to chains-per-CTA flagged sequences of one query.
 __global__ void rescue_tasks_kernel(const int32_t *__restrict__ flag_count, const QDesc *__restrict__ qd,
                                     int32_t nq, int64_t stride, int32_t warps_per_cta, int32_t units_per_task,
@@ -91,6 +129,20 @@ cudaError_t launch_build_profiles(const uint8_t *qres, const QDesc *qd, int32_t 
     const int chunk = (int)std::min<int64_t>(65535, nq - done);
     dim3 grid(8, chunk);
     build_profiles_kernel<<<grid, 256, 0, s>>>(qres, qd + done, submat, pad, prof);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    done += chunk;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_build_pair_profiles(const uint8_t *qres, const QDesc *qd, int32_t npairs, const int8_t *submat,
+                                       int32_t pad, uint8_t *prof, cudaStream_t s) {
+  int64_t done = 0;
+  while (done < npairs) {  // grid.y is limited to 65535
+    const int chunk = (int)std::min<int64_t>(65535, npairs - done);
+    dim3 grid(16, chunk);
+    build_pair_profiles_kernel<<<grid, 256, 0, s>>>(qres, qd + done, submat, pad, prof);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     done += chunk;

@@ -121,6 +121,66 @@ def test_packed_overflow_is_rescued_exactly(api):
     pq.close()
 
 
+def _prepared(api, db_seqs, q_seqs, mode, sm=BLOSUM62, go=10, ge=2, opts=None):
+    db = api.Database.from_sequences(db_seqs)
+    pq = api.PreparedQueries(db, q_seqs.residues, q_seqs.offsets, sm, go, ge, mode, opts=opts)
+    try:
+        out = pq.search().cpu().numpy()
+        pq.status()
+        return out, pq.info()
+    finally:
+        pq.close()
+        db.close()
+
+
+@pytest.mark.parametrize("cutover", [0, 300])
+def test_query_pairs(api, cutover):
+    # packed mode pairs queries of similar length into the two 16-bit halves
+    # (one database sequence per chain); the 700- and 55-residue queries have
+    # no partner within 3/4 of their length and keep the two-sequence form, so
+    # the pair plan launches one profile build and one inter-task kernel more.
+    # cutover=300 also sends the longest units to the intra-task kernel.
+    rng = np.random.Generator(np.random.PCG64(31))
+    db, _ = _ragged(33, 401, 3, 10)
+    ql = [300, 290, 281, 250, 700, 100, 96, 55, 0, 0, 17, 16]
+    q = from_list([rng.integers(0, 20, size=L).astype(np.uint8) for L in ql])
+    exp = oracle.scores(q, db, BLOSUM62, 10, 2)
+    on, info_on = _prepared(api, db, q, "packed", opts=api.options(cutover=cutover))
+    off, info_off = _prepared(api, db, q, "packed", opts=api.options(cutover=cutover, query_pairs=False))
+    _assert_equal(on, exp)
+    _assert_equal(off, exp)
+    assert info_on[3] == info_off[3] + 2
+
+
+def test_query_pairs_only_where_no_lane_can_overflow(api):
+    # +60 matches: 3,000-residue queries can pass 32767 against the 1,500-
+    # residue database units, so they stay in the rescued two-sequence form;
+    # the 40-residue pair cannot and is paired.  Scores stay exact.
+    rng = np.random.Generator(np.random.PCG64(12))
+    sm = np.full((20, 20), -5, dtype=np.int8)
+    np.fill_diagonal(sm, 60)
+    base = rng.integers(0, 20, size=3000).astype(np.uint8)
+    seqs = [rng.integers(0, 20, size=int(rng.integers(20, 300))).astype(np.uint8) for _ in range(150)]
+    seqs[7] = base[:1500].copy()
+    seqs[8] = base[1000:2500].copy()
+    db = from_list(seqs)
+    q = from_list([base, base[::-1].copy(), base[:40].copy(), rng.integers(0, 20, size=38).astype(np.uint8)])
+    exp = oracle.scores(q, db, sm, 10, 2)
+    assert exp.max() > 32767
+    got, info = _prepared(api, db, q, "packed", sm=sm, opts=api.options(cutover=4096))
+    _assert_equal(got, exp)
+
+
+@pytest.mark.parametrize("R", [4, 8, 24])
+def test_query_pairs_tiles(api, R):
+    # pairs at every rows-per-lane instance, chunks of several L*R rows
+    db, _ = _ragged(40 + R, 257, 3, 10)
+    rng = np.random.Generator(np.random.PCG64(R))
+    q = from_list([rng.integers(0, 20, size=L).astype(np.uint8) for L in (900, 880, 333, 300, 5, 4)])
+    got = _search(api, db, q, "packed", opts=api.options(rows_per_lane=R))
+    _assert_equal(got, oracle.scores(q, db, BLOSUM62, 10, 2))
+
+
 @pytest.fixture(scope="module")
 def homologs():
     w = make_workload("homologs_8k")
