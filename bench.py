@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=600,
                     help="requests of the serving run (Poisson 50/s, 500,000-protein database); 0 skips it")
     ap.add_argument("--mode", default="packed", choices=["packed", "int32"], help="form of the timed search")
+    ap.add_argument("--no-query-pairs", action="store_true",
+                    help="packed mode: keep every query in the two-sequences-per-chain form")
     ap.add_argument("--queries", type=int, default=0, help="use only the first K queries (profiling runs)")
     ap.add_argument("--db-limit", type=int, default=0, help="use only the first N database sequences (profiling runs)")
     return ap.parse_args()
@@ -303,7 +305,8 @@ def run_ours(args, w):
     db_s = w["db"]
     cells = float(q.total) * float(db_s.total)
     db = api.Database.from_sequences(db_s)
-    pq = api.PreparedQueries(db, q.residues, q.offsets, BLOSUM62, 10, 2, args.mode)
+    opts = api.options(query_pairs=not args.no_query_pairs)
+    pq = api.PreparedQueries(db, q.residues, q.offsets, BLOSUM62, 10, 2, args.mode, opts=opts)
     pq.set_timing(True)
     out = torch.empty((len(q), len(db_s)), dtype=torch.int32, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")  # > 129 MB L2

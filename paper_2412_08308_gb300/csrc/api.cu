@@ -431,7 +431,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
     d.L = pick_lanes(std::max(1, d.m), 32);
     const int LR = d.L * R;
     d.nchunks = std::max(1, (d.m + LR - 1) / LR);
-    d.chunk_stride = (int32_t)round_up(LR, 128);
+    d.chunk_stride = (int32_t)round_up((int64_t)profile_slots(d.L) * R, 128);
     d.chunk_bytes = pair_of[q] < 0 ? kProfRows * d.chunk_stride : 0;
     d.prof_off = prof;
     d.qoff = q_offsets[q];
@@ -443,6 +443,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
     chunked |= d.chunk_bytes > 0 && d.nchunks > 1;
   }
   // pair plans: 4-byte entries; at most 512 rows per chunk keeps two CTAs per SM
+  // (a residue row holds 32 lane slots of R words)
   Q->qdp.resize(Q->npairs);
   for (int64_t p = 0; p < Q->npairs; ++p) {
     QDesc &d = Q->qdp[p];
@@ -455,7 +456,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
     d.L = pick_lanes(std::max(1, d.m), std::max(4, std::min(32, 512 / R)));
     const int LR = d.L * R;
     d.nchunks = std::max(1, (d.m + LR - 1) / LR);
-    d.chunk_stride = (int32_t)round_up(4 * LR, 128);
+    d.chunk_stride = (int32_t)round_up(4 * (int64_t)profile_slots(d.L) * R, 128);
     d.chunk_bytes = kProfRows * d.chunk_stride;
     d.prof_off = prof;
     d.qoff = q_offsets[d.qa];
@@ -476,7 +477,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
       d.L = 32 * w;
       const int LR = d.L * Ri;
       d.nchunks = std::max(1, (d.m + LR - 1) / LR);
-      d.chunk_stride = (int32_t)round_up(LR, 128);
+      d.chunk_stride = (int32_t)round_up((int64_t)profile_slots(d.L) * Ri, 128);
       d.chunk_bytes = kProfRows * d.chunk_stride;
       d.prof_off = prof;
       d.qoff = q_offsets[q];

@@ -87,6 +87,25 @@ __device__ __forceinline__ uint32_t word_of(const uint4 &v, int i) {
   return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
 }
 
+// One 32-bit word of two 16-bit cells (Eqs. 1-3 per half).  hd is H of the
+// diagonal neighbour, p the substitution scores; E (this row) and f (passed
+// down the column) are updated in place, S keeps the running best.  Five
+// maxima (the zero floor rides on the first) and four per-half additions;
+// H - Go is shared by the E and F updates.  (Computing the next F from
+// max(hd + p, E, 0) - Go instead of H - Go, which is equal because
+// Ge <= Go, shortens the chain down the column but costs a fifth addition
+// and measured slower.)
+__device__ __forceinline__ uint32_t cell_word(uint32_t hd, uint32_t p, uint32_t &E, uint32_t &f, uint32_t &S,
+                                              const Consts &cs) {
+  const uint32_t tt = __vimax_s16x2_relu(__vadd2(hd, p), E);  // max(hd + SM, E, 0)
+  const uint32_t h = __vmaxs2(tt, f);
+  S = __vmaxs2(S, h);
+  const uint32_t hgo = __vsub2(h, cs.goW);
+  E = __vmaxs2(__vsub2(E, cs.geW), hgo);
+  f = __vmaxs2(__vsub2(f, cs.geW), hgo);
+  return h;
+}
+
 template <int FORM>
 using Word = typename std::conditional<FORM != kFormInt32, uint32_t, int32_t>::type;
 
@@ -135,13 +154,9 @@ __device__ __forceinline__ void column_step(LaneState<R, FORM> &st, const uint8_
     uint32_t hd = (uint32_t)st.hdiag, f = (uint32_t)inF, s = (uint32_t)S;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const uint32_t x = __vadd2(hd, pw[r]);
-      const uint32_t tt = __vimax_s16x2_relu(x, (uint32_t)st.E[r]);
-      const uint32_t h = __vmaxs2(tt, f);
-      s = __vmaxs2(s, h);
-      const uint32_t hgo = __vsub2(h, cs.goW);
-      st.E[r] = (W)__vmaxs2(__vsub2((uint32_t)st.E[r], cs.geW), hgo);
-      f = __vmaxs2(__vsub2(f, cs.geW), hgo);
+      uint32_t e = (uint32_t)st.E[r];
+      const uint32_t h = cell_word(hd, pw[r], e, f, s, cs);
+      st.E[r] = (W)e;
       hd = (uint32_t)st.Hl[r];
       st.Hl[r] = (W)h;
     }
@@ -157,20 +172,17 @@ __device__ __forceinline__ void column_step(LaneState<R, FORM> &st, const uint8_
   if constexpr (PACKED) {
     uint32_t pb[R / 4];
     load_prof<R>(prow + (res >> 16) * stride, pb);
-    uint32_t hd = (uint32_t)st.hdiag, f = (uint32_t)inF;
+    uint32_t hd = (uint32_t)st.hdiag, f = (uint32_t)inF, s = (uint32_t)S;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const uint32_t p = prmt(pa[r >> 2], pb[r >> 2], sel_pair(r & 3));  // (SM_a, SM_b), signed halves
-      const uint32_t x = __vadd2(hd, p);                                  // FMA pipe
-      const uint32_t tt = __vimax_s16x2_relu(x, (uint32_t)st.E[r]);      // max(x, E, 0)
-      const uint32_t h = __vmaxs2(tt, f);
-      S = (W)__vmaxs2((uint32_t)S, h);
-      const uint32_t hgo = __vsub2(h, cs.goW);
-      st.E[r] = (W)__vmaxs2(__vsub2((uint32_t)st.E[r], cs.geW), hgo);
-      f = __vmaxs2(__vsub2(f, cs.geW), hgo);
+      uint32_t e = (uint32_t)st.E[r];
+      const uint32_t h = cell_word(hd, p, e, f, s, cs);
+      st.E[r] = (W)e;
       hd = (uint32_t)st.Hl[r];
       st.Hl[r] = (W)h;
     }
+    S = (W)s;
     outH = st.Hl[R - 1];
     outF = (W)f;
   } else {

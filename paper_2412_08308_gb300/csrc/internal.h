@@ -41,6 +41,13 @@ struct QDesc {
   int64_t qoffb;
 };
 
+// Lane slots per profile row.  A chain of L <= 32 lanes shares its warp with
+// 32/L - 1 other chains of the same query; the profile row holds one copy of
+// the L lanes' entries per chain, so lane l of the warp reads slot l and the
+// 32 lanes touch 32 distinct slots (no shared-memory bank conflict).  Chains
+// of more than 32 lanes (the intra-task kernel) use one slot per lane.
+__host__ __device__ inline int profile_slots(int L) { return L >= 32 ? L : (32 / L) * L; }
+
 // Forms of the dynamic-programming kernels.
 constexpr int kFormInt32 = 0;   // one database sequence per chain, 32-bit cells
 constexpr int kFormPacked = 1;  // two database sequences per chain, 16-bit halves

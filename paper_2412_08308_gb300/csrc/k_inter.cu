@@ -46,7 +46,8 @@ constexpr int kRingBytes = 320;       // residues: 2 slots x 2 seqs x 16 B; boun
 // One pass of a chain over all columns of its unit for the rows of one chunk.
 template <int R, int FORM>
 __device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, const int stride, const int L,
-                                           const int k, const int lane, const bool live, const int nblk,
+                                           const int k, const int lane, const int slot, const int gstride,
+                                           const bool live, const int nblk,
                                            const int npad, const int npa, const int npb,
                                            const uint8_t *__restrict__ resA, const uint8_t *__restrict__ resB,
                                            uint8_t *ring, uint2 *gb, const bool prev, const bool next,
@@ -65,9 +66,8 @@ __device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, cons
   const bool tail = live && (k == L - 1) && next;
   uint8_t *rres = ring;                                  // [slot][seq][16 B]
   uint2 *rgb = reinterpret_cast<uint2 *>(ring + 64);     // [slot][16]
-  // query pairs: lane k's word groups sit at k*16 + i*L*16 (lanes interleaved)
-  const uint8_t *prow = FORM == kFormQPair ? pch + k * 16 : pch + k * R;
-  const int gstride = L * 16;
+  // this lane's profile slot: R bytes, or (query pairs) R/4 16-byte groups gstride apart
+  const uint8_t *prow = FORM == kFormQPair ? pch + slot * 16 : pch + slot * R;
 
   auto prefetch = [&](int blk) {
     const int slot = blk & 1;
@@ -178,6 +178,9 @@ __global__ void __launch_bounds__(kThreads, 2) inter_kernel(const InterArgs a) {
     const int k = lane - cw * L;
     const int ci = warp * G + cw;
     const bool live = (cw < G) && (ci < tk.unit_count);
+    // profile slot (lanes of chains past the last one reuse an in-range slot)
+    const int slot = cw < G ? lane : k;
+    const int gstride = profile_slots(L) * 16;
     int posA = 0, posB = 0, npa = 0, npb = 0;
     if (live) {
       const int u = tk.unit_begin + ci;
@@ -215,7 +218,8 @@ __global__ void __launch_bounds__(kThreads, 2) inter_kernel(const InterArgs a) {
         if (threadIdx.x == 0) atomicExch(a.status, SW_ETIMEOUT);
         return;
       }
-      chain_pass<R, FORM>(pbuf + b * a.pbuf_bytes, qd.chunk_stride, L, k, lane, live, nblk, npad, npa, npb,
+      chain_pass<R, FORM>(pbuf + b * a.pbuf_bytes, qd.chunk_stride, L, k, lane, slot, gstride, live, nblk, npad,
+                          npa, npb,
                             resA, resB, ring, gb, c > 0, c + 1 < qd.nchunks, cs, S);
       __syncthreads();
       if (threadIdx.x == 0 && c + 2 < qd.nchunks) issue(c + 2);

@@ -8,8 +8,10 @@ namespace {
 // database residue): signed byte P[c][i] = SM(Q[i], c) for residue c = 0..19
 // and query row i; the pad residue (c = 20) and rows past the query end hold
 // `pad` = min(0, min SM).  Layout per query: nchunks chunks, each
-// [21][chunk_stride] bytes, chunk c covering rows c*L*R .. c*L*R + L*R - 1 at
-// byte offsets 0 .. L*R-1 of each residue row; bytes past L*R hold `pad` too.
+// [21][chunk_stride] bytes, chunk c covering rows c*L*R .. c*L*R + L*R - 1.
+// A residue row holds profile_slots(L) slots of R bytes; slot s serves lane
+// k = s mod L, i.e. rows k*R .. k*R + R - 1 of the chunk.  Bytes past the
+// last slot hold `pad` too.
 __global__ void build_profiles_kernel(const uint8_t *__restrict__ qres, const QDesc *__restrict__ qd,
                                       const int8_t *__restrict__ submat, int32_t pad,
                                       uint8_t *__restrict__ prof) {
@@ -19,6 +21,7 @@ __global__ void build_profiles_kernel(const uint8_t *__restrict__ qres, const QD
   const QDesc d = qd[blockIdx.y];
   const uint8_t *q = qres + d.qoff;
   const int LR = d.L * d.R;
+  const int slots = profile_slots(d.L);
   const int64_t words = (int64_t)d.nchunks * d.chunk_bytes / 4;
   uint32_t *out = reinterpret_cast<uint32_t *>(prof + d.prof_off);
   for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words; w += (int64_t)gridDim.x * blockDim.x) {
@@ -30,10 +33,10 @@ __global__ void build_profiles_kernel(const uint8_t *__restrict__ qres, const QD
     uint32_t v = 0;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
-      const int xx = xb + b;
-      const int row = c * LR + xx;
+      const int slot = (xb + b) / d.R;
+      const int row = c * LR + (slot % d.L) * d.R + (xb + b - slot * d.R);
       int32_t val = pad;
-      if (xx < LR && row < d.m && rho < kAlphabet) val = sm[q[row] * kAlphabet + rho];
+      if (slot < slots && row < d.m && rho < kAlphabet) val = sm[q[row] * kAlphabet + rho];
       v |= ((uint32_t)val & 0xffu) << (8 * b);
     }
     out[w] = v;
@@ -43,11 +46,12 @@ __global__ void build_profiles_kernel(const uint8_t *__restrict__ qres, const QD
 // Query-pair profile: the same table for two queries qa and qb, one 32-bit
 // entry per (residue, row) holding SM(Qa[i], c) in the low and SM(Qb[i], c) in
 // the high 16-bit half (both sign-extended).  Rows past a query's own end,
-// the pad residue and entries past L*R hold `pad`.  Layout per pair: nchunks
-// chunks of [21][chunk_stride] bytes.  Within a residue row the lanes'
-// four-word groups are interleaved: row x = k*R + 4*i + j of the chunk (lane
-// k, group i, word j) sits at word (i*L + k)*4 + j, so the lanes of a warp
-// read consecutive 16-byte groups.
+// the pad residue and unused entries hold `pad`.  Layout per pair: nchunks
+// chunks of [21][chunk_stride] bytes.  Within a residue row the lane slots'
+// four-word groups are interleaved: with S = profile_slots(L) slots, word j of
+// group i of slot s sits at word (i*S + s)*4 + j and holds row
+// (s mod L)*R + 4*i + j of the chunk, so the lanes of a warp read 32
+// consecutive 16-byte groups.
 __global__ void build_pair_profiles_kernel(const uint8_t *__restrict__ qres, const QDesc *__restrict__ qd,
                                            const int8_t *__restrict__ submat, int32_t pad,
                                            uint8_t *__restrict__ prof) {
@@ -58,6 +62,7 @@ __global__ void build_pair_profiles_kernel(const uint8_t *__restrict__ qres, con
   const uint8_t *qa = qres + d.qoff;
   const uint8_t *qb = qres + d.qoffb;
   const int LR = d.L * d.R;
+  const int slots = profile_slots(d.L);
   const int64_t words = (int64_t)d.nchunks * d.chunk_bytes / 4;
   uint32_t *out = reinterpret_cast<uint32_t *>(prof + d.prof_off);
   for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words; w += (int64_t)gridDim.x * blockDim.x) {
@@ -66,11 +71,10 @@ __global__ void build_pair_profiles_kernel(const uint8_t *__restrict__ qres, con
     const int rem = (int)(x0 - (int64_t)c * d.chunk_bytes);
     const int rho = rem / d.chunk_stride;
     const int wi = (rem - rho * d.chunk_stride) / 4;
-    const int gi = wi / (4 * d.L), kk = (wi >> 2) - gi * d.L;
-    const int xx = kk * d.R + 4 * gi + (wi & 3);
-    const int row = c * LR + xx;
+    const int gi = wi / (4 * slots), slot = (wi >> 2) - gi * slots;
+    const int row = c * LR + (slot % d.L) * d.R + 4 * gi + (wi & 3);
     int32_t va = pad, vb = pad;
-    if (wi < LR && rho < kAlphabet) {
+    if (wi < slots * d.R && rho < kAlphabet) {
       if (row < d.ma) va = sm[qa[row] * kAlphabet + rho];
       if (row < d.mb) vb = sm[qb[row] * kAlphabet + rho];
     }

@@ -145,7 +145,7 @@ extern "C" int sw_search_noalloc(const sw_db *db, const uint8_t *query, int64_t 
   d.L = L;
   d.R = R;
   d.nchunks = 1;
-  d.chunk_stride = (int32_t)round_up((size_t)L * R, 128);
+  d.chunk_stride = (int32_t)round_up((size_t)profile_slots(L) * R, 128);
   d.chunk_bytes = kProfRows * d.chunk_stride;
   d.prof_off = 0;
   d.qoff = 0;
