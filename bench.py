@@ -170,11 +170,17 @@ def dp_kernel_traffic():
         rec = json.load(open(path))
     except (OSError, ValueError):
         return None
-    src = os.path.join(ROOT, "paper_2412_08308_gb300", "csrc", "k_inter.cu")
-    sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
-    if rec.get("source_sha1") != sha:
+    if rec.get("source_sha1") != dp_kernel_source_sha1():
         return None
     return rec.get("dram_bytes_per_launch")
+
+
+def dp_kernel_source_sha1():
+    """SHA-1 over the sources that define the inter-task DP kernel."""
+    h = hashlib.sha1()
+    for f in ("k_inter.cu", "dp_common.cuh", "internal.h", "devutil.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2412_08308_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
 
 
 # ----------------------------------------------------------------------------
@@ -337,7 +343,9 @@ def run_ours(args, w):
     achieved_gops = cells / k_mean / 1e9 * ALU_OPS_PER_CELL[args.mode]
     roofline = {"bound": "alu", "achieved": round(achieved_gops, 1), "peak": round(peak_gops, 1),
                 "unit": "Gop/s", "frac": round(achieved_gops / peak_gops, 4), "traffic": dp_kernel_traffic(),
-                "kernel": "inter_kernel<R, %s>" % args.mode, "alu_ops_per_cell": ALU_OPS_PER_CELL[args.mode],
+                "kernel": ("inter_kernel, 16-bit forms (query pairs; two sequences per chain for unpaired queries)"
+                           if args.mode == "packed" else "inter_kernel, int32 form"),
+                "alu_ops_per_cell": ALU_OPS_PER_CELL[args.mode],
                 "peak_basis": f"{n_sm} SMs x {ALU_LANES_PER_SM_CLK} ALU-pipe lanes/clk x {sm_mhz:.0f} MHz "
                               "(sm_max_mhz of MEASURED_PEAKS.json)",
                 "kernel_gcups": round(cells / k_mean / 1e9, 1)}
@@ -392,7 +400,7 @@ def run_ours(args, w):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        g, threads, c, dt = oracle_sample_gcups(w, 2000)
+        g, threads, c, dt = oracle_sample_gcups(w, 8000)
         cpu = {"value": round(g, 3), "unit": "GCUPS", "cores": threads, "kind": "oracle",
                "sample": f"all {len(q)} queries x 2,000 seeded database sequences ({c:.3g} cells, {dt:.1f} s)"}
 
