@@ -402,7 +402,7 @@ def run_ours(args, w):
     if rank == 0 and not args.no_cpu_baseline:
         g, threads, c, dt = oracle_sample_gcups(w, 8000)
         cpu = {"value": round(g, 3), "unit": "GCUPS", "cores": threads, "kind": "oracle",
-               "sample": f"all {len(q)} queries x 2,000 seeded database sequences ({c:.3g} cells, {dt:.1f} s)"}
+               "sample": f"all {len(q)} queries x 8,000 seeded database sequences ({c:.3g} cells, {dt:.1f} s)"}
 
     if rank == 0:
         wl = WORKLOAD if not (args.queries or args.db_limit) else (
