@@ -95,7 +95,7 @@ typedef struct sw_options {
                               residues use the intra-task (multi-warp) kernel; 0 = 2048;
                               a value above every length sends everything inter-task */
   int32_t rows_per_lane;   /* query rows per lane of the inter-task kernel: 4, 8, 12, 16 or 24;
-                              0 = 16, or 8 for batches too small to fill the GPU */
+                              0 = 24, or 8 for batches too small to fill the GPU */
   int32_t lanes_per_chain; /* lanes per chain of the inter-task kernel, 4..32; 0 = chosen per query */
   int32_t intra_rows;      /* query rows per lane of the intra-task kernel: 8 or 16; 0 = 16 */
   int32_t query_pairs;     /* packed mode, inter-task kernel: 0 = pair queries of similar length

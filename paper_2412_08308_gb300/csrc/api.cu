@@ -96,6 +96,7 @@ struct sw_queries {
   bool inter_may_flag = false;  // some packed inter-task pair can exceed the 16-bit threshold
   int grid = 1, rgrid = 1, igrid = 1, pgrid = 1, threads = 256;
   int pbuf_bytes = 0, ipbuf_bytes = 0, ppbuf_bytes = 0;
+  int pbuf_count = 2, ppbuf_count = 2;  // profile buffers of the two inter-task launches
   size_t smem = 0, ismem = 0, psmem = 0;
   int32_t gbuf_stride = 0, igbuf_stride = 0;
   int64_t long_stride = 1;
@@ -132,9 +133,11 @@ struct sw_queries {
 namespace {
 
 // Lanes per chain for one query at R rows per lane: minimise padded rows x
-// pipeline fill x idle lanes, with a small charge per chunk for the
-// boundary strip and the CTA barrier.
-int choose_lanes(int m, int R, double mean_n, int Lmax = 32) {
+// steps per column (fill[L], below) x idle lanes, with a small charge per
+// chunk for the boundary strip and the CTA barrier.  (Against the measured
+// time of the 20-query benchmark with L forced to 4..32, this model is
+// proportional to within 1.5 %.)
+int choose_lanes(int m, int R, const double *fill, int Lmax = 32) {
   int bestL = 4;
   double best = 1e300;
   for (int L = 4; L <= Lmax; ++L) {
@@ -143,8 +146,7 @@ int choose_lanes(int m, int R, double mean_n, int Lmax = 32) {
     const double rows = (double)C * LR;
     const int G = 32 / L;
     const double lane_eff = (double)(G * L) / 32.0;
-    const double fill = (mean_n + L - 1 + 8) / std::max(1.0, mean_n);
-    const double cost = rows * fill / lane_eff * (1.0 + 0.01 * C);
+    const double cost = rows * fill[L] / lane_eff * (1.0 + 0.001 * C);
     if (cost < best - 1e-9) {
       best = cost;
       bestL = L;
@@ -286,7 +288,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   for (int i = 0; i < 3; ++i)
     if (o.reserved[i]) return fail(SW_EINVAL, "sw_queries_prepare: reserved option fields must be 0");
   if (o.query_pairs != 0 && o.query_pairs != 1) return fail(SW_EINVAL, "sw_queries_prepare: query_pairs must be 0 or 1");
-  int R = o.rows_per_lane ? o.rows_per_lane : 16;
+  int R = o.rows_per_lane ? o.rows_per_lane : 24;
   const int Ri = o.intra_rows ? o.intra_rows : 16;
   const int forceL = o.lanes_per_chain;
   const int cutover = o.cutover > 0 ? o.cutover : 2048;
@@ -345,7 +347,20 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   for (int64_t u = n_long; u < Q->n_units; ++u) sum_short += unit_len(u);
   if (n_long < Q->n_units) max_short = unit_len(n_long);
   if (n_long) max_long = unit_len(0);
-  const double mean_n = Q->n_units > n_long ? std::max(16.0, sum_short / (Q->n_units - n_long)) : 16.0;
+  // fill[L]: steps a chain of L lanes spends per real column of a short unit.
+  // A pass over a unit of n padded columns takes n + L - 1 steps rounded up to
+  // whole 16-column blocks.
+  double fill[33];
+  {
+    std::vector<int64_t> hist(max_short / kColBlock + 1, 0);
+    for (int64_t u = n_long; u < Q->n_units; ++u) ++hist[unit_len(u) / kColBlock];
+    for (int L = 0; L <= 32; ++L) {
+      double steps = 0;
+      for (size_t b = 1; b < hist.size(); ++b)
+        steps += (double)hist[b] * (double)((b * kColBlock + L - 1 + kColBlock - 1) / kColBlock * kColBlock);
+      fill[L] = sum_short > 0 ? steps / sum_short : 1.0;
+    }
+  }
 
   // --- rows per lane and CTA size of the inter-task kernel.  A small batch
   // (few units x queries) cannot fill the GPU with 16-row lanes: halve the
@@ -356,7 +371,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
     double lanes = 0;
     for (int64_t q = 0; q < n_queries; ++q) {
       const int m = std::max<int>(1, (int)(q_offsets[q + 1] - q_offsets[q]));
-      lanes += (double)n_short * (forceL ? forceL : choose_lanes(m, rr, mean_n));
+      lanes += (double)n_short * (forceL ? forceL : choose_lanes(m, rr, fill));
     }
     return lanes;
   };
@@ -370,7 +385,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   auto pick_lanes = [&](int m, int Lmax) {
     if (forceL) return std::min(forceL, Lmax);
     if (latency_bound) return std::min(Lmax, std::max(4, (m + R - 1) / R));
-    return choose_lanes(m, R, mean_n, Lmax);
+    return choose_lanes(m, R, fill, Lmax);
   };
   int warps = inter_threads() / 32;
   for (; warps > 2; warps /= 2) {
@@ -442,8 +457,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
     maxc = std::max(maxc, d.chunk_bytes);
     chunked |= d.chunk_bytes > 0 && d.nchunks > 1;
   }
-  // pair plans: 4-byte entries; at most 512 rows per chunk keeps two CTAs per SM
-  // (a residue row holds 32 lane slots of R words)
+  // pair plans: 4-byte entries (a residue row holds 32 lane slots of R words)
   Q->qdp.resize(Q->npairs);
   for (int64_t p = 0; p < Q->npairs; ++p) {
     QDesc &d = Q->qdp[p];
@@ -453,7 +467,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
     d.mb = qlen(d.qb);
     d.m = std::max(d.ma, d.mb);
     d.R = R;
-    d.L = pick_lanes(std::max(1, d.m), std::max(4, std::min(32, 512 / R)));
+    d.L = pick_lanes(std::max(1, d.m), 32);
     const int LR = d.L * R;
     d.nchunks = std::max(1, (d.m + LR - 1) / LR);
     d.chunk_stride = (int32_t)round_up(4 * (int64_t)profile_slots(d.L) * R, 128);
@@ -554,8 +568,13 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   Q->n_rtask_cap = Q->inter_may_flag ? rcap : 0;
 
   // --- launch geometry
-  Q->smem = inter_smem_bytes(Q->pbuf_bytes, threads);
-  Q->psmem = inter_smem_bytes(Q->ppbuf_bytes, threads);
+  // two CTAs per SM need at most (228 KB - 2 x 1 KB reserved) / 2 of shared
+  // memory each: drop to one profile buffer where two would not fit
+  const size_t kTwoCtaSmem = 113 * 1024;
+  Q->pbuf_count = inter_smem_bytes(Q->pbuf_bytes, 2, threads) <= kTwoCtaSmem ? 2 : 1;
+  Q->ppbuf_count = inter_smem_bytes(Q->ppbuf_bytes, 2, threads) <= kTwoCtaSmem ? 2 : 1;
+  Q->smem = inter_smem_bytes(Q->pbuf_bytes, Q->pbuf_count, threads);
+  Q->psmem = inter_smem_bytes(Q->ppbuf_bytes, Q->ppbuf_count, threads);
   Q->ismem = intra_smem_bytes(Q->ipbuf_bytes);
   if (Q->smem > 200 * 1024 || Q->psmem > 200 * 1024 || (n_long && Q->ismem > 220 * 1024)) {
     delete Q;
@@ -766,6 +785,7 @@ int sw_search_prepared(const sw_db *db, const sw_queries *Q, int32_t *scores_dev
     p.n_tasks = w + Q->zero_words() + 3;
     p.task_counter = w + 6;
     p.pbuf_bytes = Q->ppbuf_bytes;
+    p.pbuf_count = Q->ppbuf_count;
     p.gbuf = Q->d_gbuf;
     p.gbuf_stride = Q->gbuf_stride;
     p.flag_count = nullptr;
@@ -779,6 +799,7 @@ int sw_search_prepared(const sw_db *db, const sw_queries *Q, int32_t *scores_dev
     a.n_tasks = w + Q->zero_words();
     a.task_counter = w + 0;
     a.pbuf_bytes = Q->pbuf_bytes;
+    a.pbuf_count = Q->pbuf_count;
     a.gbuf = Q->d_gbuf;
     a.gbuf_stride = Q->gbuf_stride;
     a.flag_count = w + 8;

@@ -81,6 +81,7 @@ struct InterArgs {
   int32_t *task_counter;    // device word, zeroed before launch
   const uint8_t *prof;      // profile chunks (see QDesc)
   int32_t pbuf_bytes;       // shared-memory bytes per profile buffer (>= every chunk_bytes)
+  int32_t pbuf_count;       // inter-task kernel: 2 = next chunk loads while the current one is in use, 1 = in turn
   uint2 *gbuf;              // chunk boundary scratch, per (CTA, chain slot): gbuf_stride entries
   int32_t gbuf_stride;
   int32_t *out;             // [nq][out_stride] scores in caller order
@@ -96,7 +97,7 @@ struct InterArgs {
 int inter_threads();
 int inter_chains_per_cta(int L);
 bool inter_supported_R(int R);
-size_t inter_smem_bytes(int pbuf_bytes, int threads);
+size_t inter_smem_bytes(int pbuf_bytes, int pbuf_count, int threads);
 cudaError_t launch_inter(const InterArgs &a, int R, int form, int grid, int threads, size_t smem,
                          cudaStream_t s);
 // Raises the instantiation's shared-memory limit (plan time only) and returns resident CTAs per SM

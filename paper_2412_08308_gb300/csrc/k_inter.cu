@@ -149,7 +149,8 @@ __global__ void __launch_bounds__(kThreads, 2) inter_kernel(const InterArgs a) {
   uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
   volatile int *s_task = reinterpret_cast<volatile int *>(smem + 16);
   uint8_t *pbuf = smem + 128;
-  uint8_t *rings = pbuf + 2 * a.pbuf_bytes;
+  uint8_t *rings = pbuf + a.pbuf_count * a.pbuf_bytes;
+  const bool dbl = a.pbuf_count == 2;
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
@@ -198,19 +199,19 @@ __global__ void __launch_bounds__(kThreads, 2) inter_kernel(const InterArgs a) {
     uint2 *gb = a.gbuf + ((size_t)blockIdx.x * nwarps * kChainsPerWarpMax + cslot) * (size_t)a.gbuf_stride;
 
     auto issue = [&](int c) {
-      const int b = c & 1;
+      const int b = dbl ? (c & 1) : 0;
       mbar_arrive_expect_tx(&mbar[b], (uint32_t)qd.chunk_bytes);
       bulk_g2s(pbuf + b * a.pbuf_bytes, a.prof + qd.prof_off + (int64_t)c * qd.chunk_bytes,
                (uint32_t)qd.chunk_bytes, &mbar[b]);
     };
     if (threadIdx.x == 0) {
       issue(0);
-      if (qd.nchunks > 1) issue(1);
+      if (dbl && qd.nchunks > 1) issue(1);
     }
 
     W S = (W)0;
     for (int c = 0; c < qd.nchunks; ++c) {
-      const int b = c & 1;
+      const int b = dbl ? (c & 1) : 0;
       const bool ok = mbar_wait_bounded(&mbar[b], b ? par1 : par0);
       if (b) par1 ^= 1u;
       else par0 ^= 1u;
@@ -222,7 +223,9 @@ __global__ void __launch_bounds__(kThreads, 2) inter_kernel(const InterArgs a) {
                           npa, npb,
                             resA, resB, ring, gb, c > 0, c + 1 < qd.nchunks, cs, S);
       __syncthreads();
-      if (threadIdx.x == 0 && c + 2 < qd.nchunks) issue(c + 2);
+      // the buffer just used is free: load the chunk after the one in flight
+      // (one buffer: the next chunk, while the other CTA on this SM computes)
+      if (threadIdx.x == 0 && c + (dbl ? 2 : 1) < qd.nchunks) issue(c + (dbl ? 2 : 1));
     }
 
     // max over the chain's lanes
@@ -263,8 +266,8 @@ int inter_chains_per_cta(int L) { return (kThreads / 32) * (32 / L); }
 int inter_ring_bytes() { return kRingBytes; }
 int inter_chains_per_warp_slots() { return kChainsPerWarpMax; }
 
-size_t inter_smem_bytes(int pbuf_bytes, int threads) {
-  return 128 + 2 * (size_t)pbuf_bytes + (size_t)(threads / 32) * kChainsPerWarpMax * kRingBytes;
+size_t inter_smem_bytes(int pbuf_bytes, int pbuf_count, int threads) {
+  return 128 + (size_t)pbuf_count * pbuf_bytes + (size_t)(threads / 32) * kChainsPerWarpMax * kRingBytes;
 }
 
 #define SWGB_INTER_R_LIST(X) X(4) X(8) X(12) X(16) X(24)

@@ -127,7 +127,7 @@ extern "C" int sw_search_noalloc(const sw_db *db, const uint8_t *query, int64_t 
       void *p = nullptr;
       e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
       if (e != cudaSuccess) return cuda_err(e, "cudaGetSymbolAddress");
-      const size_t smem = inter_smem_bytes((int)round_up(kProfMax, 128), kNoAllocThreads);
+      const size_t smem = inter_smem_bytes((int)round_up(kProfMax, 128), 2, kNoAllocThreads);
       st.occ16 = inter_max_ctas_per_sm(16, kFormInt32, kNoAllocThreads, smem);
       st.occ24 = inter_max_ctas_per_sm(24, kFormInt32, kNoAllocThreads, smem);
       if (st.occ16 <= 0 || st.occ24 <= 0) return fail_msg(SW_ECUDA, "sw_search_noalloc: kernel configuration failed");
@@ -205,7 +205,8 @@ extern "C" int sw_search_noalloc(const sw_db *db, const uint8_t *query, int64_t 
   const int occ = R == 24 ? setup.occ24 : setup.occ16;
   const int64_t gmax = (int64_t)(sms > 0 ? sms : 1) * occ;
   const int grid = (int)(n_tasks < gmax ? n_tasks : gmax);
-  const size_t smem = inter_smem_bytes(a.pbuf_bytes, kNoAllocThreads);
+  a.pbuf_count = 2;
+  const size_t smem = inter_smem_bytes(a.pbuf_bytes, a.pbuf_count, kNoAllocThreads);
   if ((e = launch_inter(a, R, kFormInt32, grid, kNoAllocThreads, smem, s)) != cudaSuccess) return cuda_err(e, "DP kernel");
 
   int32_t status = 0;
