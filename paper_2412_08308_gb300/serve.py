@@ -54,7 +54,7 @@ class Server:
     mem_budget  device bytes the in-flight batches may hold (scores, scratch)
     """
 
-    def __init__(self, db, submat, gap_open=10, gap_extend=2, mode="packed", max_batch=16, n_streams=3,
+    def __init__(self, db, submat, gap_open=10, gap_extend=2, mode="packed", max_batch=2, n_streams=2,
                  mem_budget=8 << 30, opts=None):
         import torch
 
