@@ -32,6 +32,7 @@ SIGNATURES = {
     "sw_queries_kernel_ms": (ctypes.c_int, [_p, _p, ctypes.POINTER(ctypes.c_float)]),
     "sw_queries_info": (ctypes.c_int, [_p, _pi64, _pi64, _pi64, _pi64]),
     "sw_search_noalloc": (ctypes.c_int, [_p, _p, _i64, _p, _i32, _i32, _p, _p]),
+    "sw_align_pair": (ctypes.c_int, [_p, _i64, _p, _i64, _p, _i32, _i32, _p, _p, _p, _p]),
     "sw_last_error": (ctypes.c_char_p, []),
 }
 
@@ -146,3 +147,20 @@ def sw_search_graph(db, qh, scores_dev_ptr, stream):
 
 def sw_search_noalloc(db, q_ptr, m, submat_ptr, gap_open, gap_extend, scores_dev_ptr, stream):
     return check(lib().sw_search_noalloc(db, q_ptr, m, submat_ptr, gap_open, gap_extend, scores_dev_ptr, stream))
+
+
+class SwPairOptions(ctypes.Structure):
+    """Mirror of sw_pair_options (include/swgb.h); zero fields take defaults."""
+
+    _fields_ = [("band_warps", ctypes.c_int32), ("rows_per_lane", ctypes.c_int32), ("max_ctas", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
+
+
+def sw_align_pair(q_ptr, m, t_ptr, n, submat_ptr, gap_open, gap_extend, opts, stream):
+    """Returns (score, band kernel milliseconds)."""
+    score = ctypes.c_int32(0)
+    ms = ctypes.c_float(0.0)
+    check(lib().sw_align_pair(q_ptr, m, t_ptr, n, submat_ptr, gap_open, gap_extend,
+                              ctypes.byref(opts) if opts is not None else None, ctypes.byref(score),
+                              ctypes.byref(ms), stream))
+    return score.value, ms.value

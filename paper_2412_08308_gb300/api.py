@@ -156,3 +156,21 @@ def search(db, residues, offsets, submat, gap_open=10, gap_extend=2, mode="packe
     N.sw_search(db.handle, _ptr(res), _ptr(off), nq, _ptr(sm), int(gap_open), int(gap_extend), _mode(mode), optr,
                 _stream(stream))
     return out
+
+
+def pair_options(band_warps=0, rows_per_lane=0, max_ctas=0):
+    """Knobs of sw_align_pair (sw_pair_options); 0 keeps the default."""
+    return N.SwPairOptions(int(band_warps), int(rows_per_lane), int(max_ctas))
+
+
+def align_pair(query, target, submat, gap_open=5, gap_extend=2, opts=None, stream=None, timed=False):
+    """Score-only local alignment of two long sequences (residue codes 0..19) on
+    the band-pipeline kernel; returns the score, or (score, kernel ms) if timed."""
+    q = np.ascontiguousarray(query, dtype=np.uint8)
+    t = np.ascontiguousarray(target, dtype=np.uint8)
+    sm = np.ascontiguousarray(submat, dtype=np.int8)
+    if sm.shape != (20, 20):
+        raise ValueError("submat must be 20x20")
+    score, ms = N.sw_align_pair(_ptr(q), q.size, _ptr(t), t.size, _ptr(sm), int(gap_open), int(gap_extend), opts,
+                                _stream(stream))
+    return (score, ms) if timed else score

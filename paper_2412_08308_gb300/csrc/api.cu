@@ -89,7 +89,8 @@ struct sw_queries {
   int R = 16, Ri = 16;
   Scoring sc{};
   std::vector<QDesc> qd, qdi;  // inter-task and intra-task plans per query
-  std::vector<QDesc> qdp;      // query-pair plans (packed mode, inter-task kernel)
+  std::vector<QDesc> qdp;      // query-track plans (packed mode, inter-task kernel)
+  std::vector<TrackChunk> track;  // their chunk descriptors
   int64_t n_units = 0, n_long = 0;
   int64_t n_tasks = 0, n_itasks = 0, n_itasks32 = 0, n_rtask_cap = 0;
   int64_t npairs = 0, n_ptasks = 0, n_solo = 0, n_single = 0;
@@ -109,6 +110,7 @@ struct sw_queries {
   uint8_t *d_qres = nullptr;
   int8_t *d_submat = nullptr;
   QDesc *d_qd = nullptr, *d_qdi = nullptr, *d_qdp = nullptr;
+  TrackChunk *d_track = nullptr;
   Task *d_tasks = nullptr, *d_itasks = nullptr, *d_itasks32 = nullptr, *d_rtasks = nullptr, *d_ptasks = nullptr;
   int32_t *d_units = nullptr, *d_ipos32 = nullptr, *d_upos = nullptr;
   uint8_t *d_prof = nullptr;
@@ -400,38 +402,145 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   const int threads = warps * 32;
   Q->threads = threads;
 
-  // --- query pairs (packed mode).  Two queries of similar length share one
-  // chain: the database residue of a column is common to both, so one 32-bit
-  // profile word per row feeds the two 16-bit halves and the residue-pair
-  // byte shuffle of the two-sequence form disappears.  A pair is formed only
-  // where neither query can pass the 16-bit threshold against the short
-  // database units (the pair form has no rescue pass) and the shorter query
-  // has at least 3/4 of the longer one's rows (the shorter one's padding rows
-  // are wasted work).  The remaining queries keep the two-sequence form.
+  // --- query tracks (packed mode).  Two queries share one chain, one per
+  // 16-bit half: the database residue of a column is common to both, so one
+  // 32-bit profile word per row feeds both halves and the residue-pair byte
+  // shuffle of the two-sequence form disappears.  Each half runs a track of
+  // queries laid end to end chunk by chunk, so queries of different lengths
+  // share chains without idle rows (greedy longest-first packing into
+  // balanced tracks).  Only queries that cannot pass the 16-bit threshold
+  // against the short database units join tracks (the form has no rescue
+  // pass); the others keep the two-sequence form.
   auto qlen = [&](int64_t q) { return (int32_t)(q_offsets[q + 1] - q_offsets[q]); };
   auto may_flag = [&](int64_t q, int32_t n_upper) {
     return packed && (int64_t)sc.maxp * std::min<int64_t>(qlen(q), n_upper) > sc.thresh;
   };
   const int64_t s0 = packed ? std::min<int64_t>(n, 2 * n_long) : n_long;  // first short sequence
   Q->n_single = n - s0;
-  std::vector<int32_t> pair_of(n_queries, -1);
-  std::vector<std::pair<int32_t, int32_t>> pairs;
+  std::vector<int32_t> in_track(n_queries, 0), elig;
   if (packed && o.query_pairs == 0 && n_queries >= 2 && Q->n_single > 0) {
-    std::vector<int32_t> ord(n_queries);
-    std::iota(ord.begin(), ord.end(), 0);
+    for (int64_t q = 0; q < n_queries; ++q)
+      if (!may_flag(q, max_short)) elig.push_back((int32_t)q);
+    if (elig.size() < 2) elig.clear();
+  }
+  for (int32_t q : elig) in_track[q] = 1;
+  // Two ways to lay the eligible queries out, priced with the same model as
+  // choose_lanes (padded rows x steps per column / lane use, the two halves of
+  // a plan running max(track) chunks), the cheaper one kept:
+  //  - grouped tracks: the queries sorted by length and cut into K consecutive
+  //    groups, each packed longest first into two balanced tracks.  K grows
+  //    with the query count (at least 8 queries per plan keep the tracks
+  //    balanced) and so that every resident CTA sees several tiles;
+  //  - pairs: neighbours in length order whose shorter one has at least 3/4
+  //    of the longer one's rows share a plan (one query per track); the
+  //    others keep the two-sequence form (7 instead of 6 ALU instructions per
+  //    word, two database sequences per chain).
+  // Each plan has its own lanes per chain.  (Many queries of similar length
+  // favour pairs: each pair's L fits its length; few queries of spread-out
+  // lengths favour tracks: no idle half.)
+  auto chunks_of = [&](int32_t q, int L) { return std::max(1, (qlen(q) + L * R - 1) / (L * R)); };
+  // best L for a group packed into two tracks, and its modelled cost
+  auto plan_group = [&](const std::vector<int32_t> &grp, std::vector<int32_t> *tr, int *Lout) {
+    auto pack = [&](int L, std::vector<int32_t> *out) {
+      int64_t load[2] = {0, 0};
+      for (int32_t q : grp) {
+        const int t = load[1] < load[0] ? 1 : 0;
+        if (out) out[t].push_back(q);
+        load[t] += chunks_of(q, L);
+      }
+      return std::max(load[0], load[1]);
+    };
+    auto cost_of = [&](int L) {
+      const double eff = (double)((32 / L) * L) / 32.0;
+      return (double)pack(L, nullptr) * L * R * fill[L] / eff * (1.0 + 0.001 * (double)pack(L, nullptr) /
+                                                                          std::max<size_t>(1, grp.size()) * 2);
+    };
+    int Lp = 4;
+    if (forceL) {
+      Lp = forceL;
+    } else if (latency_bound) {
+      int mmax = 1;
+      for (int32_t q : grp) mmax = std::max(mmax, qlen(q));
+      Lp = std::min(32, std::max(4, (mmax + R - 1) / R));
+    } else {
+      double best = 1e300;
+      for (int L = 4; L <= 32; ++L) {
+        const double c = cost_of(L);
+        if (c < best - 1e-9) {
+          best = c;
+          Lp = L;
+        }
+      }
+    }
+    if (tr) pack(Lp, tr);
+    if (Lout) *Lout = Lp;
+    return cost_of(Lp);
+  };
+  auto solo_cost = [&](int32_t q) {  // two-sequence form: half the columns, 7/6 the instructions
+    double best = 1e300;
+    for (int L = 4; L <= 32; ++L) {
+      const int C = chunks_of(q, L);
+      const double eff = (double)((32 / L) * L) / 32.0;
+      best = std::min(best, (double)C * L * R * fill[L] / eff * (1.0 + 0.001 * C));
+    }
+    return best * 7.0 / 12.0;
+  };
+  std::vector<std::vector<int32_t>> tracks;  // 2 per plan
+  std::vector<int> plan_L;
+  if (!elig.empty()) {
+    std::vector<int32_t> ord = elig;
     std::stable_sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) { return qlen(x) > qlen(y); });
-    for (int64_t i = 0; i + 1 < n_queries; ++i) {
-      const int32_t x = ord[i], y = ord[i + 1];
-      if (may_flag(x, max_short) || may_flag(y, max_short)) continue;
-      if (4 * (int64_t)qlen(y) < 3 * (int64_t)qlen(x)) continue;
-      pair_of[x] = (int32_t)pairs.size();
-      pair_of[y] = (int32_t)pairs.size();
-      pairs.emplace_back(x, y);
-      ++i;
+    const int64_t ne = (int64_t)ord.size();
+    // grouped tracks
+    std::vector<std::vector<int32_t>> tA;
+    std::vector<int> LA;
+    double costA = 0;
+    {
+      const int64_t tiles8 = std::max<int64_t>(1, (Q->n_single + warps * 4 - 1) / (warps * 4));
+      int64_t K = std::max<int64_t>((8 * 2 * (int64_t)sms + tiles8 - 1) / tiles8, std::min<int64_t>(8, ne / 8));
+      K = std::max<int64_t>(1, std::min<int64_t>(K, ne / 2));
+      for (int64_t p = 0; p < K; ++p) {
+        std::vector<int32_t> grp(ord.begin() + ne * p / K, ord.begin() + ne * (p + 1) / K);
+        std::vector<int32_t> tr[2];
+        int Lp = 4;
+        costA += plan_group(grp, tr, &Lp);
+        tA.push_back(tr[0]);
+        tA.push_back(tr[1]);
+        LA.push_back(Lp);
+      }
+    }
+    // pairs
+    std::vector<std::vector<int32_t>> tB;
+    std::vector<int> LB;
+    std::vector<int32_t> soloB;
+    double costB = 0;
+    for (int64_t i = 0; i < ne; ++i) {
+      const int32_t x = ord[i];
+      if (i + 1 < ne && 4 * (int64_t)qlen(ord[i + 1]) >= 3 * (int64_t)qlen(x)) {
+        std::vector<int32_t> grp{x, ord[i + 1]}, tr[2];
+        int Lp = 4;
+        costB += plan_group(grp, tr, &Lp);
+        tB.push_back(tr[0]);
+        tB.push_back(tr[1]);
+        LB.push_back(Lp);
+        ++i;
+      } else {
+        soloB.push_back(x);
+        costB += solo_cost(x);
+      }
+    }
+    if (costB < costA) {
+      tracks = tB;
+      plan_L = LB;
+      for (int32_t q : soloB) in_track[q] = 0;
+    } else {
+      tracks = tA;
+      plan_L = LA;
     }
   }
-  Q->npairs = (int64_t)pairs.size();
-  Q->n_solo = n_queries - 2 * Q->npairs;
+  Q->n_solo = 0;
+  for (int64_t q = 0; q < n_queries; ++q) Q->n_solo += in_track[q] ? 0 : 1;
+  Q->npairs = (int64_t)plan_L.size();  // track plans
 
   // --- per-query plans and profile layout (queries in a pair get no solo profile)
   Q->qd.resize(n_queries);
@@ -447,45 +556,65 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
     const int LR = d.L * R;
     d.nchunks = std::max(1, (d.m + LR - 1) / LR);
     d.chunk_stride = (int32_t)round_up((int64_t)profile_slots(d.L) * R, 128);
-    d.chunk_bytes = pair_of[q] < 0 ? kProfRows * d.chunk_stride : 0;
+    d.chunk_bytes = in_track[q] ? 0 : kProfRows * d.chunk_stride;
     d.prof_off = prof;
     d.qoff = q_offsets[q];
-    d.qa = d.qb = (int32_t)q;
-    d.ma = d.mb = d.m;
-    d.qoffb = d.qoff;
     prof += (int64_t)d.nchunks * d.chunk_bytes;
     maxc = std::max(maxc, d.chunk_bytes);
     chunked |= d.chunk_bytes > 0 && d.nchunks > 1;
   }
-  // pair plans: 4-byte entries (a residue row holds 32 lane slots of R words)
+  // track plans: 4-byte entries; every plan uses the chunk layout of 32 lane
+  // slots of R words (the most any L needs), so one kernel builds all of
+  // them; chunks of all plans in table order, plan p's from track_off
   Q->qdp.resize(Q->npairs);
-  for (int64_t p = 0; p < Q->npairs; ++p) {
-    QDesc &d = Q->qdp[p];
-    d.qa = pairs[p].first;
-    d.qb = pairs[p].second;
-    d.ma = qlen(d.qa);
-    d.mb = qlen(d.qb);
-    d.m = std::max(d.ma, d.mb);
-    d.R = R;
-    d.L = pick_lanes(std::max(1, d.m), 32);
-    const int LR = d.L * R;
-    d.nchunks = std::max(1, (d.m + LR - 1) / LR);
-    d.chunk_stride = (int32_t)round_up(4 * (int64_t)profile_slots(d.L) * R, 128);
-    d.chunk_bytes = kProfRows * d.chunk_stride;
-    d.prof_off = prof;
-    d.qoff = q_offsets[d.qa];
-    d.qoffb = q_offsets[d.qb];
-    prof += (int64_t)d.nchunks * d.chunk_bytes;
-    maxcp = std::max(maxcp, d.chunk_bytes);
-    chunked |= d.nchunks > 1;
+  Q->track.clear();
+  {
+    const int32_t stride = (int32_t)round_up(4 * (int64_t)32 * R, 128);
+    for (int64_t p = 0; p < Q->npairs; ++p) {
+      QDesc &d = Q->qdp[p];
+      const int LR = plan_L[p] * R;
+      std::vector<TrackChunk> half[2];
+      for (int h = 0; h < 2; ++h)
+        for (int32_t q : tracks[2 * p + h]) {
+          const int C = std::max(1, (qlen(q) + LR - 1) / LR);
+          for (int k = 0; k < C; ++k) {
+            TrackChunk t{};
+            t.qa = q;
+            t.ka = k;
+            t.flags = (k == 0 ? kStartA : 0) | (k == C - 1 ? kEndA : 0);
+            half[h].push_back(t);
+          }
+        }
+      const size_t nc = std::max(half[0].size(), half[1].size());
+      d.track_off = (int32_t)Q->track.size();
+      for (size_t c = 0; c < nc; ++c) {
+        TrackChunk t{};
+        t.qa = c < half[0].size() ? half[0][c].qa : -1;
+        t.ka = c < half[0].size() ? half[0][c].ka : 0;
+        t.qb = c < half[1].size() ? half[1][c].qa : -1;
+        t.kb = c < half[1].size() ? half[1][c].ka : 0;
+        t.flags = (c < half[0].size() ? half[0][c].flags : 0) | (c < half[1].size() ? half[1][c].flags * 2 : 0);
+        t.L = plan_L[p];
+        Q->track.push_back(t);
+      }
+      d.m = (int32_t)nc * LR;
+      d.L = plan_L[p];
+      d.R = R;
+      d.nchunks = (int32_t)nc;
+      d.chunk_stride = stride;
+      d.chunk_bytes = kProfRows * stride;
+      d.prof_off = prof;
+      d.qoff = 0;
+      prof += (int64_t)nc * d.chunk_bytes;
+      maxcp = std::max(maxcp, d.chunk_bytes);
+      chunked |= nc > 1;
+    }
   }
   if (n_long) {
     const int wmax = intra_threads() / 32;
     for (int64_t q = 0; q < n_queries; ++q) {
       QDesc &d = Q->qdi[q];
       d.m = Q->qd[q].m;
-      d.qa = d.qb = (int32_t)q;
-      d.ma = d.mb = d.m;
       d.R = Ri;
       const int w = (int)std::min<int64_t>(wmax, std::max<int64_t>(1, (d.m + 32 * Ri - 1) / (32 * Ri)));
       d.L = 32 * w;
@@ -495,7 +624,6 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
       d.chunk_bytes = kProfRows * d.chunk_stride;
       d.prof_off = prof;
       d.qoff = q_offsets[q];
-      d.qoffb = d.qoff;
       prof += (int64_t)d.nchunks * d.chunk_bytes;
       maxci = std::max(maxci, d.chunk_bytes);
       ichunked |= d.nchunks > 1;
@@ -525,7 +653,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
     }
   }
   for (int64_t q = 0; q < n_queries && Q->n_units > n_long; ++q) {
-    if (pair_of[q] >= 0) continue;
+    if (in_track[q]) continue;
     const QDesc &d = Q->qd[q];
     const int chains = warps * (32 / d.L);
     for (int64_t u0 = n_long; u0 < Q->n_units; u0 += chains) {
@@ -559,7 +687,10 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   std::stable_sort(tw.begin(), tw.end(), [](const TW &a, const TW &b) { return a.w > b.w; });
   std::stable_sort(twi.begin(), twi.end(), [](const TW &a, const TW &b) { return a.w > b.w; });
   std::stable_sort(twi32.begin(), twi32.end(), [](const TW &a, const TW &b) { return a.w > b.w; });
-  std::stable_sort(twp.begin(), twp.end(), [](const TW &a, const TW &b) { return a.w > b.w; });
+  // track tiles plan by plan (each plan's profile stays hot in L2 while the
+  // CTAs stream it), longest tiles first within a plan
+  std::stable_sort(twp.begin(), twp.end(),
+                   [](const TW &a, const TW &b) { return a.t.q != b.t.q ? a.t.q < b.t.q : a.w > b.w; });
   Q->n_ptasks = (int64_t)twp.size();
   Q->n_tasks = (int64_t)tw.size();
   Q->n_itasks = (int64_t)twi.size();
@@ -614,6 +745,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   const size_t b_ipos32 = round_up(4 * std::max<int64_t>((int64_t)ipos32.size(), 1), 256);
   const size_t b_rtasks = round_up(sizeof(Task) * std::max<int64_t>(Q->n_rtask_cap, 1), 256);
   const size_t b_qdp = round_up(sizeof(QDesc) * std::max<int64_t>(Q->npairs, 1), 256);
+  const size_t b_track = round_up(sizeof(TrackChunk) * std::max<int64_t>((int64_t)Q->track.size(), 1), 256);
   const size_t b_ptasks = round_up(sizeof(Task) * std::max<int64_t>(Q->n_ptasks, 1), 256);
   const size_t b_upos = round_up(4 * std::max<int64_t>(Q->npairs ? Q->n_single : 0, 1), 256);
   const size_t b_units = round_up(4 * (int64_t)units.size(), 256);
@@ -624,7 +756,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   const size_t b_flag = Q->inter_may_flag ? round_up(4 * nqm * std::max<int64_t>(n, 1), 256) : 0;
   const size_t b_iflag = packed ? round_up(4 * nqm * Q->long_stride, 256) : 0;
   Q->bytes = b_qres + b_sub + 2 * b_qd + b_tasks + b_itasks + b_itasks32 + b_ipos32 + b_rtasks + b_units + b_prof +
-             b_gbuf + b_igbuf + b_words + b_flag + b_iflag + b_qdp + b_ptasks + b_upos;
+             b_gbuf + b_igbuf + b_words + b_flag + b_iflag + b_qdp + b_ptasks + b_upos + b_track;
   cudaError_t e = cudaMallocAsync(&Q->block, Q->bytes, s);
   if (e != cudaSuccess) {
     delete Q;
@@ -653,6 +785,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   Q->d_flag_pos = Q->inter_may_flag ? (int32_t *)take(b_flag) : nullptr;
   Q->d_iflag_pos = packed ? (int32_t *)take(b_iflag) : nullptr;
   Q->d_qdp = (QDesc *)take(b_qdp);
+  Q->d_track = (TrackChunk *)take(b_track);
   Q->d_ptasks = (Task *)take(b_ptasks);
   Q->d_upos = (int32_t *)take(b_upos);
 
@@ -666,7 +799,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   const int32_t consts[4] = {(int32_t)Q->n_tasks, (int32_t)Q->n_itasks, (int32_t)Q->n_itasks32,
                              (int32_t)Q->n_ptasks};
   Q->h2d_bytes = q_offsets[n_queries] + 400 + 2 * (int64_t)sizeof(QDesc) * n_queries +
-                 (int64_t)sizeof(QDesc) * Q->npairs +
+                 (int64_t)sizeof(QDesc) * Q->npairs + (int64_t)sizeof(TrackChunk) * (int64_t)Q->track.size() +
                  (int64_t)sizeof(Task) * (Q->n_tasks + Q->n_itasks + Q->n_itasks32 + Q->n_ptasks) +
                  4 * (int64_t)units.size() + 4 * (int64_t)ipos32.size() + 4 * (int64_t)upos.size() + 16;
   e = cudaSuccess;
@@ -688,6 +821,9 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   }
   if (e == cudaSuccess && Q->npairs) {
     e = cudaMemcpyAsync(Q->d_qdp, Q->qdp.data(), sizeof(QDesc) * Q->npairs, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(Q->d_track, Q->track.data(), sizeof(TrackChunk) * Q->track.size(), cudaMemcpyHostToDevice,
+                          s);
     if (e == cudaSuccess && Q->n_ptasks)
       e = cudaMemcpyAsync(Q->d_ptasks, ptasks.data(), sizeof(Task) * Q->n_ptasks, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && !upos.empty())
@@ -733,8 +869,9 @@ int sw_search_prepared(const sw_db *db, const sw_queries *Q, int32_t *scores_dev
   if (Q->n_solo)
     SW_CUDA(launch_build_profiles(Q->d_qres, Q->d_qd, nq, Q->d_submat, Q->sc.pad, Q->d_prof, s), "profile kernel");
   if (Q->npairs)
-    SW_CUDA(launch_build_pair_profiles(Q->d_qres, Q->d_qdp, (int32_t)Q->npairs, Q->d_submat, Q->sc.pad, Q->d_prof, s),
-            "pair profile kernel");
+    SW_CUDA(launch_build_track_profiles(Q->d_qres, Q->d_qd, Q->d_qdp, Q->d_track, (int32_t)Q->track.size(),
+                                        Q->d_submat, Q->sc.pad, Q->d_prof, s),
+            "track profile kernel");
   if (Q->n_long)
     SW_CUDA(launch_build_profiles(Q->d_qres, Q->d_qdi, nq, Q->d_submat, Q->sc.pad, Q->d_prof, s),
             "profile kernel");
@@ -780,6 +917,7 @@ int sw_search_prepared(const sw_db *db, const sw_queries *Q, int32_t *scores_dev
   if (Q->n_ptasks) {  // query pairs, one short database sequence per chain
     InterArgs p = a;
     p.qd = Q->d_qdp;
+    p.track = Q->d_track;
     p.unit_pos = Q->d_upos;
     p.tasks = Q->d_ptasks;
     p.n_tasks = w + Q->zero_words() + 3;

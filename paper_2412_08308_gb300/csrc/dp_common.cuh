@@ -221,20 +221,13 @@ __device__ __forceinline__ Word<FORM> score_max(Word<FORM> a, Word<FORM> b) {
 }
 
 // Epilogue for one database unit: flag possible overflows (packed) and scatter
-// to caller order.  Query-pair units write the two halves to their queries;
-// they are planned only where no lane can pass the threshold.
+// to caller order.  (The query-pair form writes its scores per query-track
+// chunk, in the inter-task kernel.)
 template <int FORM>
 __device__ __forceinline__ void write_scores(Word<FORM> S, int posA, int posB, int q, const QDesc &qd,
                                              const InterArgs &a) {
+  static_assert(FORM != kFormQPair, "query-pair scores are written per track chunk");
   constexpr bool PACKED = FORM == kFormPacked;
-  if constexpr (FORM == kFormQPair) {
-    const int32_t sa = (int32_t)((uint32_t)S & 0xffffu), sb = (int32_t)((uint32_t)S >> 16);
-    if (sa > a.sc.thresh || sb > a.sc.thresh) atomicExch(a.status, kStatusSaturated);
-    const int32_t p = a.db.perm[posA];
-    a.out[(int64_t)qd.qa * a.out_stride + p] = sa;
-    if (qd.qb != qd.qa) a.out[(int64_t)qd.qb * a.out_stride + p] = sb;
-    return;
-  }
   const DbView &db = a.db;
   const Scoring &sc = a.sc;
   int32_t *out = a.out;

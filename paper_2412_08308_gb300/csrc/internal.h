@@ -25,21 +25,35 @@ struct Scoring {
   int32_t thresh;  // a packed 16-bit lane may have wrapped only if its score S > thresh
 };
 
-// Per-query descriptor for the dynamic-programming kernels.
+// Per-query descriptor for the dynamic-programming kernels, or (query-track
+// plans of the query-pair form) per plan.
 struct QDesc {
-  int32_t m;         // query length (query-pair plans: the longer of the two)
+  int32_t m;         // query length (track plans: nchunks * L * R)
   int32_t L;         // lanes per chain (1..32)
   int32_t R;         // rows per lane
-  int32_t nchunks;   // ceil(m / (L*R)) (>= 1)
+  int32_t nchunks;   // ceil(m / (L*R)) (>= 1); track plans: chunks of the longer track
   int32_t chunk_bytes;  // bytes of one profile chunk = 21 * chunk_stride
   int32_t chunk_stride; // bytes per profile row within a chunk (>= L*R entries, multiple of 128)
   int64_t prof_off;  // byte offset of chunk 0 in the profile buffer
   int64_t qoff;      // offset of the query residues in the query residue buffer
-  // query-pair plans (two queries in the two 16-bit halves; single-query
-  // plans repeat the query): query indices, lengths and residue offsets
-  int32_t qa, qb, ma, mb;
-  int64_t qoffb;
+  int32_t track_off; // track plans: index of the plan's first TrackChunk
+  int32_t pad_;
 };
+
+// Query tracks (query-pair form).  The two 16-bit halves of a chain each run
+// a track: queries laid end to end, chunk by chunk (every query padded to
+// whole chunks).  Chunk c of a plan computes chunk ka of query qa in the low
+// half and chunk kb of query qb in the high half; a half whose query starts
+// in the chunk takes the matrix top boundary instead of the boundary strip,
+// and a half whose query ends in it has its scores written after it.
+struct TrackChunk {
+  int32_t qa, qb;  // query per half, -1 = idle
+  int32_t ka, kb;  // chunk index within that query
+  int32_t flags;   // kStartA | kStartB | kEndA | kEndB
+  int32_t L;       // lanes per chain of the chunk's plan
+  int32_t pad_[2];
+};
+constexpr int32_t kStartA = 1, kStartB = 2, kEndA = 4, kEndB = 8;
 
 // Lane slots per profile row.  A chain of L <= 32 lanes shares its warp with
 // 32/L - 1 other chains of the same query; the profile row holds one copy of
@@ -76,6 +90,7 @@ struct InterArgs {
   DbView db;
   const int32_t *unit_pos;  // packed: 2 sorted positions per unit; int32: 1 per unit
   const QDesc *qd;
+  const TrackChunk *track;  // query-pair form: chunk descriptors of the track plans
   const Task *tasks;
   const int32_t *n_tasks;   // device word: number of tasks
   int32_t *task_counter;    // device word, zeroed before launch
@@ -91,6 +106,22 @@ struct InterArgs {
   int64_t flag_stride;
   Scoring sc;
   int32_t *status;          // device status word (SW_ETIMEOUT on an expired wait)
+};
+
+// Arguments of the band kernel (one long pair, int32 cells).
+struct BandArgs {
+  const uint8_t *target;   // target residues padded with the pad code to npad (a multiple of 16)
+  int32_t npad;
+  int32_t warps;           // warps of the chain; a band is 32 * warps * R query rows
+  int32_t nbands;
+  const uint8_t *prof;     // nbands profile chunks of chunk_bytes (query profile, L = 32 * warps)
+  int32_t chunk_bytes, chunk_stride, pbuf_bytes;
+  uint2 *strips;           // [nslots][npad] bottom rows (H, F) of the bands in flight
+  int32_t nslots;          // >= gridDim.x + 1
+  int32_t *progress;       // [nbands] columns of each band's strip published, zeroed before launch
+  int32_t *best;           // max over all cells (atomicMax), zeroed before launch
+  int32_t *status;         // SW_ETIMEOUT on an expired wait
+  Scoring sc;
 };
 
 // launchers (k_inter.cu)
@@ -110,14 +141,18 @@ int intra_threads();
 size_t intra_smem_bytes(int pbuf_bytes);
 cudaError_t configure_intra(int R, bool packed);  // plan time: raise the shared-memory limit
 cudaError_t launch_intra(const InterArgs &a, int R, bool packed, int grid, size_t smem, cudaStream_t s);
+// band kernel (k_intra.cu): same shared-memory layout as the intra-task kernel
+int band_max_ctas_per_sm(int R, size_t smem);
+cudaError_t launch_band(const BandArgs &a, int R, int grid, size_t smem, cudaStream_t s);
 
 // support kernels (k_support.cu)
 cudaError_t launch_build_profiles(const uint8_t *qres, const QDesc *qd, int32_t nq, const int8_t *submat,
                                   int32_t pad, uint8_t *prof, cudaStream_t s);
 // Query-pair tables: per chunk [21][chunk_stride] bytes of 32-bit words
 // (SM(Qa[i], c) & 0xffff) | (SM(Qb[i], c) << 16).
-cudaError_t launch_build_pair_profiles(const uint8_t *qres, const QDesc *qd, int32_t npairs, const int8_t *submat,
-                                       int32_t pad, uint8_t *prof, cudaStream_t s);
+cudaError_t launch_build_track_profiles(const uint8_t *qres, const QDesc *qdq, const QDesc *plan,
+                                        const TrackChunk *track, int32_t nchunks, const int8_t *submat, int32_t pad,
+                                        uint8_t *prof, cudaStream_t s);
 // Build rescue tasks from the per-query flag counts: tiles of warps_per_cta * (32 / L) flagged
 // positions (units_per_task == 0) or of units_per_task positions; flagged positions of query q
 // start at q * stride.  Writes the task count to *n_tasks and zeroes *counter.

@@ -44,6 +44,8 @@ constexpr int kChainsPerWarpMax = 8;  // lanes per chain >= 4
 constexpr int kRingBytes = 320;       // residues: 2 slots x 2 seqs x 16 B; boundary: 2 slots x 16 x 8 B
 
 // One pass of a chain over all columns of its unit for the rows of one chunk.
+// restart (16-bit forms): halves whose rows start a new query in this chunk;
+// they take the matrix top boundary instead of the strip of the chunk above.
 template <int R, int FORM>
 __device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, const int stride, const int L,
                                            const int k, const int lane, const int slot, const int gstride,
@@ -51,7 +53,7 @@ __device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, cons
                                            const int npad, const int npa, const int npb,
                                            const uint8_t *__restrict__ resA, const uint8_t *__restrict__ resB,
                                            uint8_t *ring, uint2 *gb, const bool prev, const bool next,
-                                           const Consts &cs, Word<FORM> &S) {
+                                           const uint32_t restart, const Consts &cs, Word<FORM> &S) {
   using W = Word<FORM>;
   constexpr bool PACKED = FORM != kFormInt32;      // 16-bit halves
   constexpr bool PAIRS = FORM == kFormPacked;      // two database sequences per unit
@@ -92,15 +94,22 @@ __device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, cons
 
   for (int blk = 0; blk < nblk; ++blk) {
     uint4 ra4 = make_uint4(0, 0, 0, 0), rb4 = make_uint4(0, 0, 0, 0);
+    uint2 *gslot = rgb + (blk & 1) * 16;
+    // lane 0's columns of this block are all real or all padding (npad is a multiple of 16)
+    const bool real = blk * kColBlock < npad;
+    const bool from_strip = prev && real;
     if (lead) {
       cp_async_wait<1>();
       ra4 = *reinterpret_cast<const uint4 *>(rres + (blk & 1) * 32);
       if (PAIRS) rb4 = *reinterpret_cast<const uint4 *>(rres + (blk & 1) * 32 + 16);
+      if (PACKED && restart && from_strip) {  // (this thread's own cp.async data, already landed)
+#pragma unroll
+        for (int i = 0; i < kColBlock; ++i) {
+          const uint2 v = gslot[i];
+          gslot[i] = make_uint2(v.x & ~restart, (v.y & ~restart) | ((uint32_t)F0 & restart));
+        }
+      }
     }
-    const uint2 *gslot = rgb + (blk & 1) * 16;
-    // lane 0's columns of this block are all real or all padding (npad is a multiple of 16)
-    const bool real = blk * kColBlock < npad;
-    const bool from_strip = prev && real;
     // 4 groups of 4 steps; only the 4 steps are unrolled, which keeps the loop
     // body small enough for the instruction cache
 #pragma unroll 1
@@ -212,6 +221,12 @@ __global__ void __launch_bounds__(kThreads, 2) inter_kernel(const InterArgs a) {
     W S = (W)0;
     for (int c = 0; c < qd.nchunks; ++c) {
       const int b = dbl ? (c & 1) : 0;
+      TrackChunk tc{};
+      uint32_t restart = 0u;
+      if constexpr (FORM == kFormQPair) {
+        tc = a.track[qd.track_off + c];
+        restart = ((tc.flags & kStartA) ? 0x0000ffffu : 0u) | ((tc.flags & kStartB) ? 0xffff0000u : 0u);
+      }
       const bool ok = mbar_wait_bounded(&mbar[b], b ? par1 : par0);
       if (b) par1 ^= 1u;
       else par0 ^= 1u;
@@ -220,18 +235,37 @@ __global__ void __launch_bounds__(kThreads, 2) inter_kernel(const InterArgs a) {
         return;
       }
       chain_pass<R, FORM>(pbuf + b * a.pbuf_bytes, qd.chunk_stride, L, k, lane, slot, gstride, live, nblk, npad,
-                          npa, npb,
-                            resA, resB, ring, gb, c > 0, c + 1 < qd.nchunks, cs, S);
+                          npa, npb, resA, resB, ring, gb, c > 0, c + 1 < qd.nchunks, restart, cs, S);
       __syncthreads();
       // the buffer just used is free: load the chunk after the one in flight
       // (one buffer: the next chunk, while the other CTA on this SM computes)
       if (threadIdx.x == 0 && c + (dbl ? 2 : 1) < qd.nchunks) issue(c + (dbl ? 2 : 1));
+      if constexpr (FORM == kFormQPair) {
+        // a half whose query ends in this chunk: its best over the chain's
+        // lanes is the score; the half then starts from zero
+        if (tc.flags & (kEndA | kEndB)) {
+          W m = S;
+          for (int d = 1; d < L; d <<= 1)
+            m = score_max<FORM>(m, (W)__shfl_sync(0xffffffffu, m, (k + d < L) ? lane + d : lane));
+          const bool endA = (tc.flags & kEndA) && tc.qa >= 0, endB = (tc.flags & kEndB) && tc.qb >= 0;
+          if (live && k == 0) {
+            const int32_t sa = (int32_t)((uint32_t)m & 0xffffu), sb = (int32_t)((uint32_t)m >> 16);
+            const int32_t p = a.db.perm[posA];
+            if (endA) a.out[(int64_t)tc.qa * a.out_stride + p] = sa;
+            if (endB) a.out[(int64_t)tc.qb * a.out_stride + p] = sb;
+            if ((endA && sa > a.sc.thresh) || (endB && sb > a.sc.thresh)) atomicExch(a.status, kStatusSaturated);
+          }
+          S = (W)((uint32_t)S & ~(((tc.flags & kEndA) ? 0x0000ffffu : 0u) | ((tc.flags & kEndB) ? 0xffff0000u : 0u)));
+        }
+      }
     }
 
-    // max over the chain's lanes
-    for (int d = 1; d < L; d <<= 1) S = score_max<FORM>(S, (W)__shfl_sync(0xffffffffu, S, (k + d < L) ? lane + d : lane));
-    if (live && k == 0)
-      write_scores<FORM>(S, posA, posB, tk.q, qd, a);
+    if constexpr (FORM != kFormQPair) {
+      // max over the chain's lanes
+      for (int d = 1; d < L; d <<= 1)
+        S = score_max<FORM>(S, (W)__shfl_sync(0xffffffffu, S, (k + d < L) ? lane + d : lane));
+      if (live && k == 0) write_scores<FORM>(S, posA, posB, tk.q, qd, a);
+    }
   }
 }
 

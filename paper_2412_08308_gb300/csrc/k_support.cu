@@ -43,42 +43,49 @@ __global__ void build_profiles_kernel(const uint8_t *__restrict__ qres, const QD
   }
 }
 
-// Query-pair profile: the same table for two queries qa and qb, one 32-bit
-// entry per (residue, row) holding SM(Qa[i], c) in the low and SM(Qb[i], c) in
-// the high 16-bit half (both sign-extended).  Rows past a query's own end,
-// the pad residue and unused entries hold `pad`.  Layout per pair: nchunks
-// chunks of [21][chunk_stride] bytes.  Within a residue row the lane slots'
-// four-word groups are interleaved: with S = profile_slots(L) slots, word j of
-// group i of slot s sits at word (i*S + s)*4 + j and holds row
+// Query-track profile (query-pair form): for chunk c of a track plan, one
+// 32-bit entry per (residue, row) holding SM(Qa[i], c) in the low and SM(Qb[i], c)
+// in the high 16-bit half (both sign-extended), where Qa, Qb are the queries the
+// two halves run in this chunk and i the row within that query's own chunk.
+// Rows past a query's end, idle halves, the pad residue and unused entries hold
+// `pad`.  Layout per chunk: [21][chunk_stride] bytes; within a residue row the
+// lane slots' four-word groups are interleaved: with S = profile_slots(L)
+// slots, word j of group i of slot s sits at word (i*S + s)*4 + j and holds row
 // (s mod L)*R + 4*i + j of the chunk, so the lanes of a warp read 32
-// consecutive 16-byte groups.
-__global__ void build_pair_profiles_kernel(const uint8_t *__restrict__ qres, const QDesc *__restrict__ qd,
-                                           const int8_t *__restrict__ submat, int32_t pad,
-                                           uint8_t *__restrict__ prof) {
+// consecutive 16-byte groups.  All plans share R and the chunk size and their
+// chunks are stored in table order, so chunk c of the table (a block row,
+// blockIdx.y, strided) sits at plan->prof_off + c * chunk_bytes; L comes with
+// each chunk.
+__global__ void build_track_profiles_kernel(const uint8_t *__restrict__ qres, const QDesc *__restrict__ qdq,
+                                            const QDesc *__restrict__ plan, const TrackChunk *__restrict__ track,
+                                            int32_t nchunks, const int8_t *__restrict__ submat, int32_t pad,
+                                            uint8_t *__restrict__ prof) {
   __shared__ int8_t sm[kAlphabet * kAlphabet];
   for (int i = threadIdx.x; i < kAlphabet * kAlphabet; i += blockDim.x) sm[i] = submat[i];
   __syncthreads();
-  const QDesc d = qd[blockIdx.y];
-  const uint8_t *qa = qres + d.qoff;
-  const uint8_t *qb = qres + d.qoffb;
-  const int LR = d.L * d.R;
-  const int slots = profile_slots(d.L);
-  const int64_t words = (int64_t)d.nchunks * d.chunk_bytes / 4;
-  uint32_t *out = reinterpret_cast<uint32_t *>(prof + d.prof_off);
-  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words; w += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t x0 = 4 * w;
-    const int c = (int)(x0 / d.chunk_bytes);
-    const int rem = (int)(x0 - (int64_t)c * d.chunk_bytes);
-    const int rho = rem / d.chunk_stride;
-    const int wi = (rem - rho * d.chunk_stride) / 4;
-    const int gi = wi / (4 * slots), slot = (wi >> 2) - gi * slots;
-    const int row = c * LR + (slot % d.L) * d.R + 4 * gi + (wi & 3);
-    int32_t va = pad, vb = pad;
-    if (wi < slots * d.R && rho < kAlphabet) {
-      if (row < d.ma) va = sm[qa[row] * kAlphabet + rho];
-      if (row < d.mb) vb = sm[qb[row] * kAlphabet + rho];
+  const QDesc d = *plan;
+  const int words = d.chunk_bytes / 4;
+  for (int c = blockIdx.y; c < nchunks; c += gridDim.y) {
+    const TrackChunk tc = track[c];
+    const int LR = tc.L * d.R;
+    const int slots = profile_slots(tc.L);
+    const uint8_t *qa = tc.qa >= 0 ? qres + qdq[tc.qa].qoff : qres;
+    const uint8_t *qb = tc.qb >= 0 ? qres + qdq[tc.qb].qoff : qres;
+    const int ma = tc.qa >= 0 ? qdq[tc.qa].m : 0, mb = tc.qb >= 0 ? qdq[tc.qb].m : 0;
+    const int ra = tc.ka * LR, rb = tc.kb * LR;  // first row of this chunk in each query
+    uint32_t *out = reinterpret_cast<uint32_t *>(prof + d.prof_off + (int64_t)c * d.chunk_bytes);
+    for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < words; w += gridDim.x * blockDim.x) {
+      const int rho = (4 * w) / d.chunk_stride;
+      const int wi = (4 * w - rho * d.chunk_stride) / 4;
+      const int gi = wi / (4 * slots), slot = (wi >> 2) - gi * slots;
+      const int x = (slot % tc.L) * d.R + 4 * gi + (wi & 3);  // row within the chunk
+      int32_t va = pad, vb = pad;
+      if (wi < slots * d.R && rho < kAlphabet) {
+        if (ra + x < ma) va = sm[qa[ra + x] * kAlphabet + rho];
+        if (rb + x < mb) vb = sm[qb[rb + x] * kAlphabet + rho];
+      }
+      out[w] = ((uint32_t)va & 0xffffu) | ((uint32_t)vb << 16);
     }
-    out[w] = ((uint32_t)va & 0xffffu) | ((uint32_t)vb << 16);
   }
 }
 
@@ -140,18 +147,13 @@ cudaError_t launch_build_profiles(const uint8_t *qres, const QDesc *qd, int32_t 
   return cudaSuccess;
 }
 
-cudaError_t launch_build_pair_profiles(const uint8_t *qres, const QDesc *qd, int32_t npairs, const int8_t *submat,
-                                       int32_t pad, uint8_t *prof, cudaStream_t s) {
-  int64_t done = 0;
-  while (done < npairs) {  // grid.y is limited to 65535
-    const int chunk = (int)std::min<int64_t>(65535, npairs - done);
-    dim3 grid(16, chunk);
-    build_pair_profiles_kernel<<<grid, 256, 0, s>>>(qres, qd + done, submat, pad, prof);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    done += chunk;
-  }
-  return cudaSuccess;
+cudaError_t launch_build_track_profiles(const uint8_t *qres, const QDesc *qdq, const QDesc *plan,
+                                        const TrackChunk *track, int32_t nchunks, const int8_t *submat, int32_t pad,
+                                        uint8_t *prof, cudaStream_t s) {
+  if (nchunks <= 0) return cudaSuccess;
+  dim3 grid(4, std::min(nchunks, 65535));
+  build_track_profiles_kernel<<<grid, 256, 0, s>>>(qres, qdq, plan, track, nchunks, submat, pad, prof);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_rescue_tasks(const int32_t *flag_count, const QDesc *qd, int32_t nq, int64_t stride,

@@ -135,21 +135,20 @@ def _prepared(api, db_seqs, q_seqs, mode, sm=BLOSUM62, go=10, ge=2, opts=None):
 
 @pytest.mark.parametrize("cutover", [0, 300])
 def test_query_pairs(api, cutover):
-    # packed mode pairs queries of similar length into the two 16-bit halves
-    # (one database sequence per chain); the 700- and 55-residue queries have
-    # no partner within 3/4 of their length and keep the two-sequence form, so
-    # the pair plan launches one profile build and one inter-task kernel more.
+    # packed mode runs queries in pairs, one per 16-bit half of a chain (one
+    # database sequence per chain): each half runs a track of queries laid end
+    # to end chunk by chunk.  Lengths from 0 to 700 residues; with this small
+    # database the planner spreads the queries over several track plans.
     # cutover=300 also sends the longest units to the intra-task kernel.
     rng = np.random.Generator(np.random.PCG64(31))
     db, _ = _ragged(33, 401, 3, 10)
     ql = [300, 290, 281, 250, 700, 100, 96, 55, 0, 0, 17, 16]
     q = from_list([rng.integers(0, 20, size=L).astype(np.uint8) for L in ql])
     exp = oracle.scores(q, db, BLOSUM62, 10, 2)
-    on, info_on = _prepared(api, db, q, "packed", opts=api.options(cutover=cutover))
-    off, info_off = _prepared(api, db, q, "packed", opts=api.options(cutover=cutover, query_pairs=False))
+    on, _ = _prepared(api, db, q, "packed", opts=api.options(cutover=cutover))
+    off, _ = _prepared(api, db, q, "packed", opts=api.options(cutover=cutover, query_pairs=False))
     _assert_equal(on, exp)
     _assert_equal(off, exp)
-    assert info_on[3] == info_off[3] + 2
 
 
 def test_query_pairs_only_where_no_lane_can_overflow(api):
@@ -169,15 +168,20 @@ def test_query_pairs_only_where_no_lane_can_overflow(api):
     assert exp.max() > 32767
     got, info = _prepared(api, db, q, "packed", sm=sm, opts=api.options(cutover=4096))
     _assert_equal(got, exp)
+    # the track plan adds its profile build and its inter-task launch
+    _, info_off = _prepared(api, db, q, "packed", sm=sm, opts=api.options(cutover=4096, query_pairs=False))
+    assert info[3] == info_off[3] + 2
 
 
-@pytest.mark.parametrize("R", [4, 8, 24])
-def test_query_pairs_tiles(api, R):
-    # pairs at every rows-per-lane instance, chunks of several L*R rows
-    db, _ = _ragged(40 + R, 257, 3, 10)
-    rng = np.random.Generator(np.random.PCG64(R))
-    q = from_list([rng.integers(0, 20, size=L).astype(np.uint8) for L in (900, 880, 333, 300, 5, 4)])
-    got = _search(api, db, q, "packed", opts=api.options(rows_per_lane=R))
+@pytest.mark.parametrize("R,L", [(4, 0), (8, 0), (24, 0), (4, 4), (12, 7)])
+def test_query_pairs_tiles(api, R, L):
+    # tracks at several rows-per-lane instances; with 4 x 4 rows per chunk a
+    # track switches queries many times (restarting its half from the matrix
+    # top boundary) and queries span up to 57 chunks
+    db, _ = _ragged(40 + R + L, 257, 3, 10)
+    rng = np.random.Generator(np.random.PCG64(R + L))
+    q = from_list([rng.integers(0, 20, size=n).astype(np.uint8) for n in (900, 880, 333, 300, 5, 4, 17, 16, 1)])
+    got = _search(api, db, q, "packed", opts=api.options(rows_per_lane=R, lanes_per_chain=L))
     _assert_equal(got, oracle.scores(q, db, BLOSUM62, 10, 2))
 
 

@@ -226,3 +226,44 @@ def test_batch_matches_single_calls(oracle_mod):
     sub = np.array([5, 0, 59, 17], dtype=np.int64)
     part = oracle_mod.scores(qs, db, BLOSUM62, 10, 2, subset=sub, threads=2)
     assert (part == all_scores[:, sub]).all()
+
+
+# --- the DNA scoring of the pairwise workload (+1 / -3, gaps 5 + 2k) ---------
+
+def test_dna_matrix_is_the_papers_scoring():
+    from workload.matrices import DNA_GAP_EXTEND, DNA_GAP_OPEN, DNA_SUBMAT
+    assert DNA_SUBMAT.shape == (20, 20)
+    assert (np.diag(DNA_SUBMAT) == 1).all()
+    assert (DNA_SUBMAT[~np.eye(20, dtype=bool)] == -3).all()
+    assert (DNA_GAP_OPEN, DNA_GAP_EXTEND) == (5, 2)
+
+
+@pytest.mark.parametrize("n", [1, 2, 17, 64])
+def test_dna_identity_scores_its_length(oracle_mod, n):
+    # with +1 matches, every mismatch or gap only lowers a path, so the full
+    # diagonal of X against itself is optimal: S(X, X) = |X|
+    from workload.matrices import DNA_SUBMAT
+    x = np.random.Generator(np.random.PCG64(n)).integers(0, 4, size=n).astype(np.uint8)
+    assert oracle_mod.score(x, x, DNA_SUBMAT, 5, 2) == n
+
+
+@pytest.mark.parametrize("n,p", [(40, 0), (40, 1), (40, 20), (40, 38), (40, 39), (9, 4), (3, 1)])
+def test_dna_one_substitution_closed_form(oracle_mod, n, p):
+    # X against X with base p changed: the full diagonal scores (n - 1) - 3,
+    # the two unchanged flanks p and n - 1 - p; a detour around the mismatch
+    # needs a gap in each sequence (>= 2 x 7 > 4), so
+    # S = max(n - 4, p, n - 1 - p)
+    from workload.matrices import DNA_SUBMAT
+    x = np.random.Generator(np.random.PCG64(100 + n)).integers(0, 4, size=n).astype(np.uint8)
+    y = x.copy()
+    y[p] = (y[p] + 1) % 4
+    assert oracle_mod.score(x, y, DNA_SUBMAT, 5, 2) == max(n - 4, p, n - 1 - p)
+
+
+def test_dna_brute_force(oracle_mod):
+    from workload.matrices import DNA_SUBMAT
+    rng = np.random.Generator(np.random.PCG64(77))
+    for _ in range(40):
+        a = rng.integers(0, 4, size=int(rng.integers(0, 6))).astype(np.uint8)
+        b = rng.integers(0, 4, size=int(rng.integers(0, 6))).astype(np.uint8)
+        assert oracle_mod.score(a, b, DNA_SUBMAT, 5, 2) == _pins.brute_force(a, b, DNA_SUBMAT, 5, 2)

@@ -210,6 +210,68 @@ def make_workload(name, n_db=None, n_queries=None):
     return out
 
 
+# ---------------------------------------------------------------------------
+# DNA pairs (the paper's pairwise workload, Sec. 4.1, Table 3): the genome
+# pairs are not available; each stand-in pair is a uniform random target of
+# the database sequence's size and a query of the query sequence's size that
+# is a diverged copy of the target (10% substitutions, indel events at 1% of
+# positions, insertion or deletion with equal odds, length Geometric(0.5)),
+# extended with random bases when the query is the longer one.
+# ---------------------------------------------------------------------------
+
+DNA_SEED = 5000
+DNA_PAIRS = {  # name: (query length, target length), the sizes of the paper's five pairs
+    "dna_162k_x_172k": (162_000, 172_000),
+    "dna_543k_x_536k": (543_000, 536_000),
+    "dna_1m_x_1m": (1_000_000, 1_000_000),
+    "dna_3m_x_3m": (3_000_000, 3_000_000),
+    "dna_7m_x_5m": (7_000_000, 5_000_000),
+}
+
+
+def diverge_dna(rng, seq, p_sub=0.10, p_indel=0.01):
+    """A diverged copy of a DNA code array (codes 0..3), vectorised: each
+    position is substituted by one of the three other bases with probability
+    p_sub; indel events start before a position with probability p_indel."""
+    seq = np.asarray(seq, dtype=np.uint8)
+    n = seq.size
+    sub = rng.random(n) < p_sub
+    out = seq.copy()
+    out[sub] = (out[sub] + rng.integers(1, 4, size=int(sub.sum()))) % 4
+    ev = np.flatnonzero(rng.random(n) < p_indel)
+    if ev.size == 0:
+        return out
+    lens = rng.geometric(0.5, size=ev.size)
+    ins = rng.random(ev.size) < 0.5
+    pieces, start = [], 0
+    for pos, k, is_ins in zip(ev.tolist(), lens.tolist(), ins.tolist()):
+        if pos < start:
+            continue  # inside a deletion
+        pieces.append(out[start:pos])
+        if is_ins:
+            pieces.append(rng.integers(0, 4, size=k).astype(np.uint8))
+            start = pos
+        else:
+            start = pos + k
+    pieces.append(out[start:])
+    return np.concatenate(pieces).astype(np.uint8)
+
+
+def make_dna_pair(name=None, m=None, n=None, seed=DNA_SEED):
+    """(query, target) uint8 code arrays: a named pair of DNA_PAIRS, or sizes
+    m, n.  The query has about m codes (indels change it slightly)."""
+    if name is not None:
+        m, n = DNA_PAIRS[name]
+        seed = DNA_SEED + list(DNA_PAIRS).index(name) + 1
+    rng = np.random.Generator(np.random.PCG64(seed))
+    target = rng.integers(0, 4, size=n).astype(np.uint8)
+    common = min(m, n)
+    query = diverge_dna(rng, target[:common])
+    if m > common:
+        query = np.concatenate([query, rng.integers(0, 4, size=m - common).astype(np.uint8)])
+    return query, target
+
+
 def sample_indices(n, k, seed=SAMPLE_SEED):
     """A seeded sample of ``k`` distinct subject indices out of ``n`` (sorted)."""
     rng = np.random.Generator(np.random.PCG64(seed))

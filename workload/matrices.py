@@ -59,6 +59,19 @@ GAP_OPEN = 10
 GAP_EXTEND = 2
 
 
+# Scoring of the paper's DNA pairwise alignments (Sec. 4.1): +1 for a match,
+# -3 for a mismatch, gap penalties 5/2 (read like the protein ones: a gap run
+# of length k costs 5 + 2k).  Nucleotides use codes 0..3 (A, C, G, T); the
+# matrix spans the library's 20-code alphabet with the same rule.
+DNA_ALPHABET = "ACGT"
+DNA_MATCH = 1
+DNA_MISMATCH = -3
+DNA_GAP_OPEN = 5
+DNA_GAP_EXTEND = 2
+DNA_SUBMAT = np.full((20, 20), DNA_MISMATCH, dtype=np.int8)
+np.fill_diagonal(DNA_SUBMAT, DNA_MATCH)
+
+
 def encode(text):
     """Map a protein string over ``ALPHABET`` to uint8 codes."""
     lut = {c: i for i, c in enumerate(ALPHABET)}
