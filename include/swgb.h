@@ -238,12 +238,12 @@ int sw_search_noalloc(const sw_db *db, const uint8_t *query, int64_t m, const in
  * pairwise alignment of two long DNA sequences, Sec. 2.2 case (a) and Sec. 4.1;
  * Eqs. 1-3 with the gap convention above), on one GPU.
  *
- * The query rows are cut into bands of 32 * band_warps * rows_per_lane rows.
- * Each band is swept across the whole target by one CTA, and band b starts on
- * a column as soon as band b-1 has finished it: the bands run as a pipeline
- * over all SMs (a cooperative launch; every wait between CTAs is bounded).
- * Cells are int32, so scores up to 2^31 - 1 are exact (a million-residue
- * identity scores 10^6 with +1 matches).
+ * The query rows are cut into bands of 32 * rows_per_lane rows, one per warp:
+ * a warp is a chain of 32 lanes that sweeps the band across the whole target,
+ * and band b starts on a column as soon as band b-1 has finished it, so the
+ * bands run as a pipeline over every warp of every SM (a cooperative launch;
+ * every wait between warps is bounded).  Cells are int32, so scores up to
+ * 2^31 - 1 are exact (a million-residue identity scores 10^6 with +1 matches).
  *
  *   query, m     host pointer to m residue codes 0..19 (DNA: any 4 or 5 of
  *                them, e.g. A C G T N = 0 1 2 3 4), m < 2^31
@@ -256,17 +256,20 @@ int sw_search_noalloc(const sw_db *db, const uint8_t *query, int64_t m, const in
  *   score        host pointer, receives S = max(0, max H)
  *   kernel_ms    host pointer or NULL: duration of the band kernel
  *   stream       stream for the work (NULL = legacy default); the call
- *                allocates its device scratch (strips of (number of CTAs + 1)
- *                x n x 8 bytes, the query profile, the target), returns when
- *                the score is in *score and frees the scratch
+ *                allocates its device scratch (the boundary rows of the bands
+ *                in flight, at most a quarter of the free memory or 8 GB, the
+ *                query profile, the target), returns when the score is in
+ *                *score and frees the scratch
  *
  * Errors: SW_EINVAL, SW_ENOMEM, SW_ECUDA, SW_ETIMEOUT.
  */
 typedef struct sw_pair_options {
-  int32_t band_warps;     /* warps of a band's chain, 1..16; 0 = 16 */
-  int32_t rows_per_lane;  /* 8 or 16; 0 = 8 */
-  int32_t max_ctas;       /* at most this many CTAs (bands in flight); 0 = all that fit */
-  int32_t reserved[5];    /* must be 0 */
+  int32_t band_warps;     /* at most this many warps (bands in flight) per CTA, 1..16; 0 = 16 */
+  int32_t rows_per_lane;  /* 8, 16 or 24 (a band is 32 x rows_per_lane query rows); 0 = 16 */
+  int32_t max_ctas;       /* at most this many CTAs; 0 = all that fit */
+  int32_t ring_columns;   /* columns each band's boundary ring holds, a multiple of 16 >= 256 (a band
+                             runs at most that far ahead of the band below); 0 = automatic */
+  int32_t reserved[4];    /* must be 0 */
 } sw_pair_options;
 
 int sw_align_pair(const uint8_t *query, int64_t m, const uint8_t *target, int64_t n, const int8_t *submat,

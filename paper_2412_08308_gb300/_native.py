@@ -153,7 +153,7 @@ class SwPairOptions(ctypes.Structure):
     """Mirror of sw_pair_options (include/swgb.h); zero fields take defaults."""
 
     _fields_ = [("band_warps", ctypes.c_int32), ("rows_per_lane", ctypes.c_int32), ("max_ctas", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("ring_columns", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 def sw_align_pair(q_ptr, m, t_ptr, n, submat_ptr, gap_open, gap_extend, opts, stream):

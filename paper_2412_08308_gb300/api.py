@@ -158,9 +158,9 @@ def search(db, residues, offsets, submat, gap_open=10, gap_extend=2, mode="packe
     return out
 
 
-def pair_options(band_warps=0, rows_per_lane=0, max_ctas=0):
+def pair_options(band_warps=0, rows_per_lane=0, max_ctas=0, ring_columns=0):
     """Knobs of sw_align_pair (sw_pair_options); 0 keeps the default."""
-    return N.SwPairOptions(int(band_warps), int(rows_per_lane), int(max_ctas))
+    return N.SwPairOptions(int(band_warps), int(rows_per_lane), int(max_ctas), int(ring_columns))
 
 
 def align_pair(query, target, submat, gap_open=5, gap_extend=2, opts=None, stream=None, timed=False):

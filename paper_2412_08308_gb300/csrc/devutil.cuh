@@ -70,4 +70,32 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// Release/acquire flags between CTAs (gpu scope).
+__device__ __forceinline__ int32_t ld_acquire(const int32_t *p) {
+  int32_t v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(int32_t *p, int32_t v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// A wait on another warp of a long pipeline, which may legitimately last as
+// long as a whole band takes: ~60 s at GB300 clocks.
+constexpr long long kLongWaitBudgetCycles = 120000000000LL;
+
+// Wait until *p >= v (published by another CTA or warp) and return the value
+// read; a value < v means the clock budget ran out.
+__device__ __forceinline__ int32_t wait_flag_value(const int32_t *p, int32_t v, long long budget) {
+  int32_t cur = ld_acquire(p);
+  if (cur >= v) return cur;
+  const long long t0 = clock64();
+  while ((cur = ld_acquire(p)) < v) {
+    if (clock64() - t0 > budget) return cur;
+    __nanosleep(128);
+  }
+  return cur;
+}
+
 }  // namespace swgb

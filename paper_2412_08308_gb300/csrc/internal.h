@@ -108,21 +108,26 @@ struct InterArgs {
   int32_t *status;          // device status word (SW_ETIMEOUT on an expired wait)
 };
 
-// Arguments of the band kernel (one long pair, int32 cells).
-struct BandArgs {
-  const uint8_t *target;   // target residues padded with the pad code to npad (a multiple of 16)
+// Arguments of the pair-band kernel (k_inter.cu): one long pair, int32 cells,
+// one band of 32 * R query rows per warp.
+struct PairBandArgs {
+  const uint8_t *target;   // target codes padded with the pad code to npad (a multiple of 16)
   int32_t npad;
-  int32_t warps;           // warps of the chain; a band is 32 * warps * R query rows
   int32_t nbands;
-  const uint8_t *prof;     // nbands profile chunks of chunk_bytes (query profile, L = 32 * warps)
-  int32_t chunk_bytes, chunk_stride, pbuf_bytes;
-  uint2 *strips;           // [nslots][npad] bottom rows (H, F) of the bands in flight
-  int32_t nslots;          // >= gridDim.x + 1
-  int32_t *progress;       // [nbands] columns of each band's strip published, zeroed before launch
+  const uint8_t *prof;     // nbands profile chunks of band_bytes = rows * stride (L = 32)
+  int32_t band_bytes, stride, pbuf_bytes;
+  uint2 *strips;           // [nslots][window] rings of bottom rows (H, F)
+  int32_t nslots;          // >= (warps of the grid) + 1, or nbands
+  int32_t window;          // columns per ring (a multiple of 16)
+  int32_t *prog, *cons;    // [nbands] columns published / consumed, zeroed before launch
   int32_t *best;           // max over all cells (atomicMax), zeroed before launch
   int32_t *status;         // SW_ETIMEOUT on an expired wait
   Scoring sc;
 };
+int pair_threads();
+size_t pair_smem_bytes(int pbuf_bytes, int warps);
+int pair_max_ctas_per_sm(int R, int threads, size_t smem);
+cudaError_t launch_pair(const PairBandArgs &a, int R, int grid, int threads, size_t smem, cudaStream_t s);
 
 // launchers (k_inter.cu)
 int inter_threads();
@@ -141,9 +146,6 @@ int intra_threads();
 size_t intra_smem_bytes(int pbuf_bytes);
 cudaError_t configure_intra(int R, bool packed);  // plan time: raise the shared-memory limit
 cudaError_t launch_intra(const InterArgs &a, int R, bool packed, int grid, size_t smem, cudaStream_t s);
-// band kernel (k_intra.cu): same shared-memory layout as the intra-task kernel
-int band_max_ctas_per_sm(int R, size_t smem);
-cudaError_t launch_band(const BandArgs &a, int R, int grid, size_t smem, cudaStream_t s);
 
 // support kernels (k_support.cu)
 cudaError_t launch_build_profiles(const uint8_t *qres, const QDesc *qd, int32_t nq, const int8_t *submat,

@@ -46,50 +46,16 @@ __device__ __forceinline__ bool wait_at_least(volatile int32_t *p, int32_t v, vo
   return true;
 }
 
-__device__ __forceinline__ int32_t ld_acquire(const int32_t *p) {
-  int32_t v;
-  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void st_release(int32_t *p, int32_t v) {
-  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Wait until another CTA has published at least v columns at *p; false on
-// timeout or when this CTA is aborting.
-__device__ __forceinline__ bool wait_published(const int32_t *p, int32_t v, volatile int32_t *abort) {
-  if (ld_acquire(p) >= v) return true;
-  const long long t0 = clock64();
-  while (ld_acquire(p) < v) {
-    if (*abort) return false;
-    if (clock64() - t0 > kWaitBudgetCycles) return false;
-    __nanosleep(64);
-  }
-  return true;
-}
-
-// Where the chain's top boundary comes from and where its bottom row goes.
-// In one CTA (intra-task kernel) both are the same per-CTA strip, separated by
-// the CTA barrier between chunks.  Across CTAs (band kernel) the strip of the
-// band above is read after its producer has published the columns
-// (prog_in), and this band publishes its own progress (prog_out).
-struct StripIO {
-  const uint2 *in;
-  uint2 *out;
-  const int32_t *prog_in;
-  int32_t *prog_out;
-};
-
 // One chunk of 32*Wq*R query rows against one database unit: the chain of
 // Wq warps sweeps all columns; warp w > 0 reads the bottom row of warp w-1
-// from the shared-memory ring, warp 0 reads the strip (prev) or the matrix
-// top boundary, and the last warp writes the strip for the next chunk (next).
-template <int R, int FORM, bool CROSS>
+// from the shared-memory ring, warp 0 reads the CTA's strip (prev) or the
+// matrix top boundary, and the last warp writes the strip for the next chunk
+// (next); the CTA barrier between chunks separates the two.
+template <int R, int FORM>
 __device__ __forceinline__ void sweep_chunk(IntraShared *sh, const uint8_t *pbuf, const int chunk_stride,
                                             uint4 *rings, const int Wq, const int warp, const int lane,
                                             const uint8_t *resA, const uint8_t *resB, const int npa, const int npb,
-                                            const int npad, const bool prev, const bool next, const StripIO io,
+                                            const int npad, const bool prev, const bool next, uint2 *gb,
                                             int32_t *status, const Consts &cs, Word<FORM> &S) {
   using W = Word<FORM>;
   constexpr bool PACKED = FORM != kFormInt32;
@@ -118,16 +84,7 @@ __device__ __forceinline__ void sweep_chunk(IntraShared *sh, const uint8_t *pbuf
       ra4n = col < npa ? *reinterpret_cast<const uint4 *>(resA + col) : padv;
       if (PACKED) rb4n = col < npb ? *reinterpret_cast<const uint4 *>(resB + col) : padv;
     }
-    if (prev && lane < kColBlock && col + lane < npad) {
-      if (CROSS && !wait_published(io.prog_in, min(col + kColBlock, npad), vabort)) {
-        if (!*vabort) {
-          *vabort = 1;
-          atomicExch(status, SW_ETIMEOUT);
-        }
-        return;
-      }
-      gvn = __ldcg(io.in + col + lane);
-    }
+    if (prev && lane < kColBlock && col + lane < npad) gvn = __ldcg(gb + col + lane);
   };
   if (first) fetch(0);
   for (int blk = 0; blk < nblk; ++blk) {
@@ -192,21 +149,16 @@ __device__ __forceinline__ void sweep_chunk(IntraShared *sh, const uint8_t *pbuf
           const int col = tau - 31;
           if (col >= 0 && col < npad) {
             if (!last) ring_out[col % kRing] = make_uint4((uint32_t)outH, (uint32_t)outF, outRes, 0u);
-            else if (next) io.out[col] = make_uint2((uint32_t)outH, (uint32_t)outF);
+            else if (next) gb[col] = make_uint2((uint32_t)outH, (uint32_t)outF);
           }
         }
       }
     }
     __syncwarp();
-    if (lane == 31) {
+    if (lane == 31 && !last) {
+      __threadfence_block();
       const int written = min(max(0, col0 + kColBlock - 31), npad);
-      if (!last) {
-        __threadfence_block();
-        *(volatile int32_t *)&sh->prod[warp] = written;
-      } else if (CROSS && next) {
-        __threadfence();
-        st_release(io.prog_out, written);
-      }
+      *(volatile int32_t *)&sh->prod[warp] = written;
     }
     if (lane == 0 && !first) *(volatile int32_t *)&sh->cons[warp] = min(col0 + kColBlock, npad);
   }
@@ -252,7 +204,6 @@ __global__ void __launch_bounds__(kIntraThreads, 1) intra_kernel(const InterArgs
     const uint8_t *resA = a.db.res + a.db.off[posA];
     const uint8_t *resB = a.db.res + a.db.off[posB];
     uint2 *gb = a.gbuf + (size_t)blockIdx.x * a.gbuf_stride;
-    const StripIO io{gb, gb, nullptr, nullptr};
 
     W S = (W)0;
     for (int c = 0; c < qd.nchunks; ++c) {
@@ -272,8 +223,8 @@ __global__ void __launch_bounds__(kIntraThreads, 1) intra_kernel(const InterArgs
         return;
       }
       if (warp < Wq)
-        sweep_chunk<R, FORM, false>(sh, pbuf, qd.chunk_stride, rings, Wq, warp, lane, resA, resB, npa, npb, npad,
-                                    c > 0, c + 1 < qd.nchunks, io, a.status, cs, S);
+        sweep_chunk<R, FORM>(sh, pbuf, qd.chunk_stride, rings, Wq, warp, lane, resA, resB, npa, npb, npad, c > 0,
+                             c + 1 < qd.nchunks, gb, a.status, cs, S);
       __syncthreads();  // chunk done: ring counters, strip and profile buffer are free
       if (*vabort) return;
     }
@@ -291,72 +242,6 @@ __global__ void __launch_bounds__(kIntraThreads, 1) intra_kernel(const InterArgs
   }
 }
 
-// Band wavefront over one long (query, target) pair (the pairwise alignment of
-// two long sequences, Sec. 2.2 case (a); Fig. 1 intra-sequence parallelism),
-// int32 cells.  Band b is rows [b*B, (b+1)*B) of the matrix (B = 32*W*R, one
-// profile chunk) and is computed by CTA b mod gridDim.x, which takes its bands
-// in order.  The band's chain sweeps every target column; its top boundary is
-// the bottom row of band b-1, read from band b-1's strip as soon as that
-// band's CTA has published the columns, so consecutive bands run as a
-// pipeline across the CTAs.  Every CTA of the cooperative launch is resident,
-// band b only waits on band b-1, and each CTA takes its bands in increasing
-// order, so the waits cannot form a cycle; each wait is still bounded.
-template <int R>
-__global__ void __launch_bounds__(kIntraThreads, 1) band_kernel(const BandArgs a) {
-  using W = Word<kFormInt32>;
-  extern __shared__ __align__(128) uint8_t smem[];
-  IntraShared *sh = reinterpret_cast<IntraShared *>(smem);
-  uint8_t *pbuf = smem + 256;
-  uint4 *rings = reinterpret_cast<uint4 *>(pbuf + a.pbuf_bytes);
-
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const Consts cs = make_consts(a.sc);
-  volatile int32_t *vabort = &sh->abort;
-  if (threadIdx.x == 0) {
-    mbar_init(&sh->mbar, 1);
-    sh->abort = 0;
-    fence_mbar_init();
-  }
-  __syncthreads();
-  uint32_t parity = 0;
-  W S = (W)0;
-  for (int b = blockIdx.x; b < a.nbands; b += gridDim.x) {
-    if (threadIdx.x < kWarpsMax) {
-      sh->prod[threadIdx.x] = 0;
-      sh->cons[threadIdx.x] = 0;
-    }
-    if (threadIdx.x == 0) {
-      mbar_arrive_expect_tx(&sh->mbar, (uint32_t)a.chunk_bytes);
-      bulk_g2s(pbuf, a.prof + (int64_t)b * a.chunk_bytes, (uint32_t)a.chunk_bytes, &sh->mbar);
-    }
-    __syncthreads();
-    const bool ok = mbar_wait_bounded(&sh->mbar, parity);
-    parity ^= 1u;
-    if (!__syncthreads_and(ok)) {
-      if (threadIdx.x == 0) atomicExch(a.status, SW_ETIMEOUT);
-      return;
-    }
-    StripIO io;
-    io.in = a.strips + (size_t)((b + a.nslots - 1) % a.nslots) * a.npad;
-    io.out = a.strips + (size_t)(b % a.nslots) * a.npad;
-    io.prog_in = a.progress + (b > 0 ? b - 1 : 0);
-    io.prog_out = a.progress + b;
-    if (warp < a.warps)
-      sweep_chunk<R, kFormInt32, true>(sh, pbuf, a.chunk_stride, rings, a.warps, warp, lane, a.target, a.target,
-                                       a.npad, 0, a.npad, b > 0, b + 1 < a.nbands, io, a.status, cs, S);
-    __syncthreads();
-    if (*vabort) return;
-  }
-  for (int d = 16; d > 0; d >>= 1) S = max(S, (W)__shfl_xor_sync(0xffffffffu, S, d));
-  if (lane == 0) sh->smax[warp] = (uint32_t)S;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    W m = (W)sh->smax[0];
-    for (int w = 1; w < kWarpsMax; ++w) m = max(m, (W)sh->smax[w]);
-    atomicMax(a.best, m);
-  }
-}
-
 template <int R, bool PACKED>
 cudaError_t launch_intra_one(const InterArgs &a, int grid, size_t smem, cudaStream_t s) {
   intra_kernel<R, PACKED><<<grid, kIntraThreads, smem, s>>>(a);
@@ -370,42 +255,9 @@ cudaError_t configure_intra_one() {
   return cudaFuncSetAttribute(intra_kernel<R, PACKED>, cudaFuncAttributeMaxDynamicSharedMemorySize, kIntraSmemMax);
 }
 
-template <int R>
-cudaError_t launch_band_one(const BandArgs &a, int grid, size_t smem, cudaStream_t s) {
-  void *args[] = {(void *)&a};
-  return cudaLaunchCooperativeKernel((const void *)band_kernel<R>, dim3(grid), dim3(kIntraThreads), args, smem, s);
-}
-
-template <int R>
-int configure_band_one(size_t smem) {
-  if (cudaFuncSetAttribute(band_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, kIntraSmemMax) !=
-      cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, band_kernel<R>, kIntraThreads, smem) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  return n;
-}
-
 }  // namespace
 
 int intra_threads() { return kIntraThreads; }
-
-int band_max_ctas_per_sm(int R, size_t smem) {
-  if (R == 8) return configure_band_one<8>(smem);
-  if (R == 16) return configure_band_one<16>(smem);
-  return 0;
-}
-
-cudaError_t launch_band(const BandArgs &a, int R, int grid, size_t smem, cudaStream_t s) {
-  if (R == 8) return launch_band_one<8>(a, grid, smem, s);
-  if (R == 16) return launch_band_one<16>(a, grid, smem, s);
-  return cudaErrorInvalidValue;
-}
 
 size_t intra_smem_bytes(int pbuf_bytes) {
   return 256 + (size_t)pbuf_bytes + (size_t)kWarpsMax * kRing * sizeof(uint4);

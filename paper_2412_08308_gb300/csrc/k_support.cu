@@ -135,10 +135,11 @@ __global__ void rescue_tasks_kernel(const int32_t *__restrict__ flag_count, cons
 cudaError_t launch_build_profiles(const uint8_t *qres, const QDesc *qd, int32_t nq, const int8_t *submat,
                                   int32_t pad, uint8_t *prof, cudaStream_t s) {
   if (nq <= 0) return cudaSuccess;
+  const int gx = (int)std::max<int64_t>(8, std::min<int64_t>(1024, 1024 / nq));  // few queries: more blocks each
   int64_t done = 0;
   while (done < nq) {  // grid.y is limited to 65535
     const int chunk = (int)std::min<int64_t>(65535, nq - done);
-    dim3 grid(8, chunk);
+    dim3 grid(gx, chunk);
     build_profiles_kernel<<<grid, 256, 0, s>>>(qres, qd + done, submat, pad, prof);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

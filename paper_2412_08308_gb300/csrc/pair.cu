@@ -1,5 +1,6 @@
 // sw_align_pair: the score of one long (query, target) pair, computed by the
-// band kernel (k_intra.cu) as a pipeline of query-row bands across all SMs.
+// pair-band kernel (k_inter.cu) as a pipeline of query-row bands, one per
+// warp, across every warp of every SM.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -82,12 +83,16 @@ extern "C" int sw_align_pair(const uint8_t *query, int64_t m, const uint8_t *tar
     return pair_fail(SW_EINVAL, "sw_align_pair: gap penalties out of range (%lld, %lld)", gap_open, gap_extend);
   sw_pair_options o{};
   if (opts) o = *opts;
-  for (int i = 0; i < 5; ++i)
+  for (int i = 0; i < 4; ++i)
     if (o.reserved[i]) return pair_fail(SW_EINVAL, "sw_align_pair: reserved option fields must be 0");
+  if (o.ring_columns != 0 && (o.ring_columns < 256 || o.ring_columns % kColBlock))
+    return pair_fail(SW_EINVAL, "sw_align_pair: ring_columns must be 0 or a multiple of 16 >= 256 (got %lld)",
+                     o.ring_columns);
   if (o.band_warps < 0 || o.band_warps > 16)
     return pair_fail(SW_EINVAL, "sw_align_pair: band_warps must be 0..16 (got %lld)", o.band_warps);
-  if (o.rows_per_lane != 0 && o.rows_per_lane != 8 && o.rows_per_lane != 16)
-    return pair_fail(SW_EINVAL, "sw_align_pair: rows_per_lane must be 0, 8 or 16 (got %lld)", o.rows_per_lane);
+  if (o.rows_per_lane != 0 && o.rows_per_lane != 8 && o.rows_per_lane != 16 && o.rows_per_lane != 24)
+    return pair_fail(SW_EINVAL, "sw_align_pair: rows_per_lane must be 0, 8, 16 or 24 (got %lld)",
+                     o.rows_per_lane);
   if (o.max_ctas < 0) return pair_fail(SW_EINVAL, "sw_align_pair: negative max_ctas");
   if (m == 0 || n == 0) return SW_OK;
 
@@ -97,37 +102,56 @@ extern "C" int sw_align_pair(const uint8_t *query, int64_t m, const uint8_t *tar
   if (e != cudaSuccess) return pair_cuda(e, "cudaGetDevice");
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
 
-  // geometry: bands of 32 * W * R query rows, one profile chunk each
-  const int W = o.band_warps ? o.band_warps : 16;
-  const int R = o.rows_per_lane ? o.rows_per_lane : 8;
-  const int L = 32 * W;
-  const int64_t B = (int64_t)L * R;
+  // geometry: bands of 32 * R query rows, one warp each; each warp stages its
+  // band's profile (21 residue rows) in shared memory
+  const int R = o.rows_per_lane ? o.rows_per_lane : 16;
+  const int64_t B = 32 * (int64_t)R;
   const int64_t nbands64 = (m + B - 1) / B;
+  if (nbands64 >= ((int64_t)1 << 31)) return pair_fail(SW_EINVAL, "sw_align_pair: too many bands");
   const int64_t npad = std::max<int64_t>(kColBlock, round_up(n, kColBlock));
   QDesc qd{};
   qd.m = (int32_t)m;
-  qd.L = L;
+  qd.L = 32;
   qd.R = R;
   qd.nchunks = (int32_t)nbands64;
-  qd.chunk_stride = (int32_t)round_up((int64_t)profile_slots(L) * R, 128);
+  qd.chunk_stride = (int32_t)round_up((int64_t)profile_slots(32) * R, 128);
   qd.chunk_bytes = kProfRows * qd.chunk_stride;
   const int pbuf_bytes = (int)round_up(qd.chunk_bytes, 128);
-  const size_t smem = intra_smem_bytes(pbuf_bytes);
-  if (smem > 220 * 1024) return pair_fail(SW_EINVAL, "sw_align_pair: band profile too large for shared memory");
-  const int occ = band_max_ctas_per_sm(R, smem);
-  if (occ <= 0) return pair_fail(SW_ECUDA, "sw_align_pair: cannot configure the band kernel");
-  int64_t grid = std::min<int64_t>(nbands64, (int64_t)sms * occ);
+  int warps = 16;
+  while (warps > 1 && pair_smem_bytes(pbuf_bytes, warps) > 200 * 1024) --warps;
+  if (o.band_warps) warps = std::min(warps, o.band_warps);
+  const int threads = 32 * warps;
+  const size_t smem = pair_smem_bytes(pbuf_bytes, warps);
+  if (smem > 200 * 1024) return pair_fail(SW_EINVAL, "sw_align_pair: band profile too large for shared memory");
+  const int occ = pair_max_ctas_per_sm(R, threads, smem);
+  if (occ <= 0) return pair_fail(SW_ECUDA, "sw_align_pair: cannot configure the pair kernel");
+  int64_t grid = std::min<int64_t>((nbands64 + warps - 1) / warps, (int64_t)sms * occ);
   if (o.max_ctas) grid = std::min<int64_t>(grid, o.max_ctas);
-  const int64_t nslots = std::min<int64_t>(nbands64, grid + 1);
+  const int64_t gw = grid * warps;
+  const int64_t nslots = std::min<int64_t>(nbands64, gw + 1);
+
+  // strip rings: whole rows when they fit a quarter of the free memory (up to
+  // 8 GB), else rings of fewer columns; a band then runs at most that many
+  // columns ahead of the band below it.  The band below may still be queued
+  // behind a band of the same round on its warp, so the first band of a
+  // round must be able to finish while each band of the round holds a full
+  // ring: rings of at least npad / (warps of the grid) columns.
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = (size_t)1 << 30;
+  const int64_t budget = std::min<int64_t>((int64_t)free_b / 4, (int64_t)8 << 30);
+  int64_t window = std::min<int64_t>(npad, budget / std::max<int64_t>(1, nslots * (int64_t)sizeof(uint2)));
+  window = std::max<int64_t>(4096, window / kColBlock * kColBlock);
+  if (o.ring_columns) window = o.ring_columns;
+  window = std::max<int64_t>(window, round_up((npad + gw - 1) / gw + 64, kColBlock));
+  window = std::min<int64_t>(window, npad);
 
   // device scratch: query, target, matrix, plan, profile, strips, progress, result words
   const size_t b_q = round_up(m, 256), b_t = round_up(npad, 256), b_sub = 512, b_qd = 256;
   const size_t b_prof = round_up(nbands64 * (int64_t)qd.chunk_bytes, 256);
-  const size_t b_strip = round_up(nslots * npad * (int64_t)sizeof(uint2), 256);
-  const size_t b_prog = round_up(4 * nbands64, 256), b_words = 256;
+  const size_t b_strip = round_up(nslots * window * (int64_t)sizeof(uint2), 256);
+  const size_t b_prog = round_up(8 * nbands64, 256), b_words = 256;
   const size_t bytes = b_q + b_t + b_sub + b_qd + b_prof + b_strip + b_prog + b_words;
-  size_t free_b = 0, total_b = 0;
-  if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && bytes > free_b)
+  if (bytes > free_b)
     return pair_fail(SW_ENOMEM, "sw_align_pair: needs %lld bytes of device memory, %lld free", (long long)bytes,
                      (long long)free_b);
   PairScratch sc;
@@ -144,7 +168,7 @@ extern "C" int sw_align_pair(const uint8_t *query, int64_t m, const uint8_t *tar
   QDesc *d_qd = (QDesc *)((uint8_t *)d_sub + b_sub);
   uint8_t *d_prof = (uint8_t *)d_qd + b_qd;
   uint2 *d_strip = (uint2 *)(d_prof + b_prof);
-  int32_t *d_prog = (int32_t *)((uint8_t *)d_strip + b_strip);
+  int32_t *d_prog = (int32_t *)((uint8_t *)d_strip + b_strip);  // [nbands] published, then [nbands] consumed
   int32_t *d_words = (int32_t *)((uint8_t *)d_prog + b_prog);  // [0] best, [1] status
 
   std::vector<uint8_t> tpad((size_t)npad, (uint8_t)kPadCode);
@@ -165,18 +189,19 @@ extern "C" int sw_align_pair(const uint8_t *query, int64_t m, const uint8_t *tar
   e = launch_build_profiles(d_q, d_qd, 1, d_sub, scr.pad, d_prof, s);
   if (e != cudaSuccess) return pair_cuda(e, "profile kernel");
 
-  BandArgs a{};
+  PairBandArgs a{};
   a.target = d_t;
   a.npad = (int32_t)npad;
-  a.warps = W;
   a.nbands = (int32_t)nbands64;
   a.prof = d_prof;
-  a.chunk_bytes = qd.chunk_bytes;
-  a.chunk_stride = qd.chunk_stride;
+  a.band_bytes = qd.chunk_bytes;
+  a.stride = qd.chunk_stride;
   a.pbuf_bytes = pbuf_bytes;
   a.strips = d_strip;
   a.nslots = (int32_t)nslots;
-  a.progress = d_prog;
+  a.window = (int32_t)window;
+  a.prog = d_prog;
+  a.cons = d_prog + nbands64;
   a.best = d_words;
   a.status = d_words + 1;
   a.sc = scr;
@@ -185,8 +210,8 @@ extern "C" int sw_align_pair(const uint8_t *query, int64_t m, const uint8_t *tar
       return pair_cuda(e, "cudaEventCreate");
     if ((e = cudaEventRecord(sc.e0, s)) != cudaSuccess) return pair_cuda(e, "event");
   }
-  e = launch_band(a, R, (int)grid, smem, s);
-  if (e != cudaSuccess) return pair_cuda(e, "band kernel");
+  e = launch_pair(a, R, (int)grid, threads, smem, s);
+  if (e != cudaSuccess) return pair_cuda(e, "pair kernel");
   if (kernel_ms && (e = cudaEventRecord(sc.e1, s)) != cudaSuccess) return pair_cuda(e, "event");
   int32_t words[2] = {0, 0};
   e = cudaMemcpyAsync(words, d_words, sizeof words, cudaMemcpyDeviceToHost, s);

@@ -1,9 +1,10 @@
 """GPU parity of the long-pair band kernel (sw_align_pair) against the CPU oracle.
 
-The band kernel cuts the query rows into bands and runs them as a pipeline
-across CTAs; the options below shrink the bands and cap the CTAs so that small
-pairs still span many bands, several bands per CTA and every kind of boundary.
-Scores are int32; the bar is equality.
+The kernel cuts the query rows into bands, one per warp, and runs them as a
+pipeline across all warps; the options below shrink the bands, cap the warps
+and the boundary rings so that small pairs still span many bands, several
+bands per warp, full rings and every kind of boundary.  Scores are int32; the
+bar is equality.
 """
 
 import numpy as np
@@ -29,22 +30,26 @@ def api():
     return _api
 
 
-@pytest.mark.parametrize("warps,rows,ctas", [(1, 8, 0), (1, 8, 3), (2, 16, 2), (3, 8, 1), (16, 8, 0), (16, 16, 0)])
-def test_related_dna_pair(api, warps, rows, ctas):
-    # a diverged copy: bands of 256..8192 rows, up to 12 bands on as few as one
-    # CTA (every band then waits on the band the same CTA computed before)
+@pytest.mark.parametrize("warps,rows,ctas,ring", [(1, 8, 0, 0), (1, 8, 3, 0), (2, 16, 2, 0), (3, 8, 1, 0),
+                                                 (16, 24, 0, 0), (16, 16, 0, 256), (2, 24, 1, 256), (1, 8, 1, 256),
+                                                 (8, 8, 1, 256)])
+def test_related_dna_pair(api, warps, rows, ctas, ring):
+    # a diverged copy: bands of 256..768 rows, one per warp; with one or a few
+    # warps in the grid each warp takes many bands in turn (every band then
+    # follows the band above it on another warp or on the same one), and
+    # 256-column boundary rings make every band wait for room
     q, t = make_dna_pair(m=3000, n=2900, seed=11)
     exp = oracle.score(q, t, DNA_SUBMAT, 5, 2)
-    got = api.align_pair(q, t, DNA_SUBMAT, 5, 2, opts=api.pair_options(warps, rows, ctas))
+    got = api.align_pair(q, t, DNA_SUBMAT, 5, 2, opts=api.pair_options(warps, rows, ctas, ring))
     assert got == exp
 
 
 def test_many_bands_several_rounds(api):
-    # 20,000 x 20,000 cells in 79 bands of 256 rows on 5 CTAs: 16 rounds of
-    # the CTA pipeline, strips reused every 6 bands
+    # 20,000 x 20,000 cells in 79 bands of 256 rows on 5 warps: 16 rounds of
+    # the warp pipeline, rings of 4,096 columns reused every 6 bands
     q, t = make_dna_pair(m=20000, n=20000, seed=12)
     exp = oracle.score(q, t, DNA_SUBMAT, 5, 2)
-    got = api.align_pair(q, t, DNA_SUBMAT, 5, 2, opts=api.pair_options(1, 8, 5))
+    got = api.align_pair(q, t, DNA_SUBMAT, 5, 2, opts=api.pair_options(1, 8, 5, 4096))
     assert got == exp
 
 
@@ -74,6 +79,7 @@ def test_protein_pair(api):
     t[1000:3000] = q[1500:3500]
     exp = oracle.score(q, t, BLOSUM62, 10, 2)
     assert api.align_pair(q, t, BLOSUM62, 10, 2, opts=api.pair_options(4, 16, 0)) == exp
+    assert api.align_pair(q, t, BLOSUM62, 10, 2) == exp
 
 
 def test_identity_at_full_size(api):
@@ -103,7 +109,8 @@ def test_invalid_arguments(api):
                  lambda: api.align_pair(x, bad, DNA_SUBMAT, 5, 2),
                  lambda: api.align_pair(x, x, DNA_SUBMAT, -1, 2),
                  lambda: api.align_pair(x, x, DNA_SUBMAT, 5, 2, opts=api.pair_options(17, 0, 0)),
-                 lambda: api.align_pair(x, x, DNA_SUBMAT, 5, 2, opts=api.pair_options(0, 12, 0))):
+                 lambda: api.align_pair(x, x, DNA_SUBMAT, 5, 2, opts=api.pair_options(0, 12, 0)),
+                 lambda: api.align_pair(x, x, DNA_SUBMAT, 5, 2, opts=api.pair_options(0, 0, 0, 128))):
         with pytest.raises(SwError) as e:
             call()
         assert e.value.code == SW_EINVAL
