@@ -431,6 +431,7 @@ int pair_threads() { return kPairThreads; }
 size_t pair_smem_bytes(int pbuf_bytes, int warps) { return (size_t)warps * (pbuf_bytes + kRingBytes); }
 
 int pair_max_ctas_per_sm(int R, int threads, size_t smem) {
+  if (R == 4) return configure_pair_one<4>(threads, smem);
   if (R == 8) return configure_pair_one<8>(threads, smem);
   if (R == 16) return configure_pair_one<16>(threads, smem);
   if (R == 24) return configure_pair_one<24>(threads, smem);
@@ -438,6 +439,7 @@ int pair_max_ctas_per_sm(int R, int threads, size_t smem) {
 }
 
 cudaError_t launch_pair(const PairBandArgs &a, int R, int grid, int threads, size_t smem, cudaStream_t s) {
+  if (R == 4) return launch_pair_one<4>(a, grid, threads, smem, s);
   if (R == 8) return launch_pair_one<8>(a, grid, threads, smem, s);
   if (R == 16) return launch_pair_one<16>(a, grid, threads, smem, s);
   if (R == 24) return launch_pair_one<24>(a, grid, threads, smem, s);

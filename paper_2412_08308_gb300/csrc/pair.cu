@@ -90,8 +90,9 @@ extern "C" int sw_align_pair(const uint8_t *query, int64_t m, const uint8_t *tar
                      o.ring_columns);
   if (o.band_warps < 0 || o.band_warps > 16)
     return pair_fail(SW_EINVAL, "sw_align_pair: band_warps must be 0..16 (got %lld)", o.band_warps);
-  if (o.rows_per_lane != 0 && o.rows_per_lane != 8 && o.rows_per_lane != 16 && o.rows_per_lane != 24)
-    return pair_fail(SW_EINVAL, "sw_align_pair: rows_per_lane must be 0, 8, 16 or 24 (got %lld)",
+  if (o.rows_per_lane != 0 && o.rows_per_lane != 4 && o.rows_per_lane != 8 && o.rows_per_lane != 16 &&
+      o.rows_per_lane != 24)
+    return pair_fail(SW_EINVAL, "sw_align_pair: rows_per_lane must be 0, 4, 8, 16 or 24 (got %lld)",
                      o.rows_per_lane);
   if (o.max_ctas < 0) return pair_fail(SW_EINVAL, "sw_align_pair: negative max_ctas");
   if (m == 0 || n == 0) return SW_OK;
@@ -104,7 +105,13 @@ extern "C" int sw_align_pair(const uint8_t *query, int64_t m, const uint8_t *tar
 
   // geometry: bands of 32 * R query rows, one warp each; each warp stages its
   // band's profile (21 residue rows) in shared memory
-  const int R = o.rows_per_lane ? o.rows_per_lane : 16;
+  // Bands in flight are the parallelism: one warp each.  Rows per lane 16
+  // once the pair has 8 bands per SM at that height, else 8 (4 bands per SM),
+  // else 4, trading work per step for bands; the warps of a CTA are the
+  // bands per SM, so that every SM gets bands.
+  auto bands_of = [&](int r) { return (m + 32 * (int64_t)r - 1) / (32 * (int64_t)r); };
+  int R = o.rows_per_lane;
+  if (!R) R = bands_of(16) >= 8 * (int64_t)sms ? 16 : bands_of(8) >= 4 * (int64_t)sms ? 8 : 4;
   const int64_t B = 32 * (int64_t)R;
   const int64_t nbands64 = (m + B - 1) / B;
   if (nbands64 >= ((int64_t)1 << 31)) return pair_fail(SW_EINVAL, "sw_align_pair: too many bands");
@@ -117,7 +124,7 @@ extern "C" int sw_align_pair(const uint8_t *query, int64_t m, const uint8_t *tar
   qd.chunk_stride = (int32_t)round_up((int64_t)profile_slots(32) * R, 128);
   qd.chunk_bytes = kProfRows * qd.chunk_stride;
   const int pbuf_bytes = (int)round_up(qd.chunk_bytes, 128);
-  int warps = 16;
+  int warps = (int)std::min<int64_t>(16, std::max<int64_t>(1, (nbands64 + sms - 1) / sms));
   while (warps > 1 && pair_smem_bytes(pbuf_bytes, warps) > 200 * 1024) --warps;
   if (o.band_warps) warps = std::min(warps, o.band_warps);
   const int threads = 32 * warps;

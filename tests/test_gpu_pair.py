@@ -32,9 +32,9 @@ def api():
 
 @pytest.mark.parametrize("warps,rows,ctas,ring", [(1, 8, 0, 0), (1, 8, 3, 0), (2, 16, 2, 0), (3, 8, 1, 0),
                                                  (16, 24, 0, 0), (16, 16, 0, 256), (2, 24, 1, 256), (1, 8, 1, 256),
-                                                 (8, 8, 1, 256)])
+                                                 (8, 8, 1, 256), (4, 4, 2, 256)])
 def test_related_dna_pair(api, warps, rows, ctas, ring):
-    # a diverged copy: bands of 256..768 rows, one per warp; with one or a few
+    # a diverged copy: bands of 128..768 rows, one per warp; with one or a few
     # warps in the grid each warp takes many bands in turn (every band then
     # follows the band above it on another warp or on the same one), and
     # 256-column boundary rings make every band wait for room
