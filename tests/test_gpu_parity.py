@@ -98,6 +98,33 @@ def test_extreme_asymmetric_matrix(api, mode):
     _assert_equal(got, oracle.scores(q, db, sm, 7, 3))
 
 
+@pytest.mark.parametrize("scale,go,ge", [(2, 20, 4), (3, 8, 1)])
+def test_wider_matrices_and_gap_schemes(api, scale, go, ge):
+    # other substitution matrices and gap schemes than BLOSUM62 10/2: a matrix
+    # scale x BLOSUM62 has entries up to 11 * scale, so the 16-bit threshold
+    # (32767 - max SM) and the overflow bound max(SM) * min(m, n) move with it.
+    # A 3,000-residue query and database copies of 1,200 and 2,400 of its
+    # residues: at scale 3 the 2,400-residue copy scores ~40,000 and is
+    # rescued (cutover 4096: inter-task) or computed in int32 (cutover 1000:
+    # intra-task).  Every form and plan, exact against the oracle.
+    rng = np.random.Generator(np.random.PCG64(60 + scale))
+    sm = (BLOSUM62.astype(np.int32) * scale).astype(np.int8)
+    base = rng.integers(0, 20, size=3000).astype(np.uint8)
+    seqs = [rng.integers(0, 20, size=int(rng.integers(10, 700))).astype(np.uint8) for _ in range(240)]
+    seqs[3] = base[:1200].copy()
+    seqs[100] = base[500:2900].copy()
+    db = from_list(seqs)
+    q = from_list([base, base[:400].copy(), rng.integers(0, 20, size=390).astype(np.uint8),
+                   rng.integers(0, 20, size=150).astype(np.uint8)])
+    exp = oracle.scores(q, db, sm, go, ge)
+    if scale == 3:
+        assert exp.max() > 32767
+    for mode in MODES:
+        for cutover in (1000, 4096):
+            got = _search(api, db, q, mode, sm=sm, go=go, ge=ge, opts=api.options(cutover=cutover))
+            _assert_equal(got, exp)
+
+
 def test_packed_overflow_is_rescued_exactly(api):
     # identity-like matrix with +60 matches: a 700-residue self match scores
     # 42000 > 32767, so the 16-bit lanes saturate and the int32 rescue must
