@@ -12,6 +12,7 @@ exposes:
 * ``score(q, d, submat, gap_open, gap_extend)``         -- one pair
 * ``score_init(..., init="zero"|"neginf")``            -- boundary-init variant
 * ``scores(queries, db, submat, gap_open, gap_extend)`` -- all pairs, int32 [nq, nd]
+* ``align(q, d, submat, gap_open, gap_extend)``          -- one optimal alignment (traceback)
 
 Gap convention: a run of k gap positions costs ``gap_open + k * gap_extend``.
 """
@@ -52,6 +53,8 @@ def _load():
         lib.oracle_sw_score.restype = i32
         lib.oracle_sw_batch.argtypes = [p, p, i64, p, p, i64, p, i64, p, i32, i32, p, i32]
         lib.oracle_sw_batch.restype = i32
+        lib.oracle_sw_align.argtypes = [p, i64, p, i64, p, i32, i32, p, p, p]
+        lib.oracle_sw_align.restype = i64
         _lib = lib
     return _lib
 
@@ -83,6 +86,23 @@ def score_init(q, d, submat, gap_open, gap_extend, init="zero"):
 
 def score(q, d, submat, gap_open, gap_extend):
     return score_init(q, d, submat, gap_open, gap_extend, "zero")
+
+
+def align(q, d, submat, gap_open, gap_extend):
+    """One optimal local alignment: (score, q_begin, q_end, t_begin, t_end, ops),
+    ops a str over M (aligned pair), I (query residue against a gap), D
+    (database residue against a gap); coordinates 0-based, ends exclusive."""
+    lib = _load()
+    q, d, sm = _u8(q), _u8(d), _sm(submat)
+    sc = ctypes.c_int32(0)
+    coords = np.zeros(4, dtype=np.int64)
+    ops = np.zeros(max(1, q.size + d.size), dtype=np.uint8)
+    k = lib.oracle_sw_align(_ptr(q), q.size, _ptr(d), d.size, _ptr(sm), int(gap_open), int(gap_extend),
+                            ctypes.byref(sc), coords.ctypes.data_as(ctypes.c_void_p), _ptr(ops))
+    if k < 0:
+        raise ValueError("invalid input to oracle")
+    return (int(sc.value), int(coords[0]), int(coords[1]), int(coords[2]), int(coords[3]),
+            bytes(ops[:k]).decode())
 
 
 def default_threads():

@@ -1,9 +1,10 @@
 /*
  * CPU oracle -- TEST INFRASTRUCTURE ONLY.
  *
- * Plain, slow, scalar int32 score-only Smith-Waterman local alignment with
- * Gotoh affine gaps, written from the recurrences of Sec. 2.2 (Eqs. 1-3) and
- * the cell-update order of Algorithm 1 (Sec. 3.2.1).  Only the tests, the
+ * Plain, slow, scalar int32 Smith-Waterman local alignment with Gotoh affine
+ * gaps, written from the recurrences of Sec. 2.2 (Eqs. 1-3) and the
+ * cell-update order of Algorithm 1 (Sec. 3.2.1): the score of a pair, of all
+ * pairs of two sets, and one optimal alignment of a pair (traceback).  Only the tests, the
  * smoke check and the benchmark's CPU-baseline leg may load this library; the
  * product path never does.  It shares no code, header or table with the GPU
  * library.
@@ -156,4 +157,80 @@ int32_t oracle_sw_batch(const uint8_t *qres, const int64_t *qoff, int64_t nq,
     for (int k = 0; k < started; ++k) pthread_join(th[k], NULL);
     free(th);
     return J.failed ? -1 : 0;
+}
+
+/* ---- one optimal local alignment (traceback), full matrices -------------
+ *
+ * The same recurrences (Eqs. 1-3, paper boundary values) kept for every cell,
+ * then a walk back from the first cell (row-major order) that holds the
+ * score S: in H, the diagonal move if H = H[i-1][j-1] + SM, else the E state
+ * if H = E, else the F state (H = F); in E, a gap opening if E = H[i][j-1] -
+ * Go, else an extension; in F likewise with H[i-1][j]; the walk ends in H on
+ * a cell with H = 0.  Operations, from the first aligned position to the
+ * last: 'M' aligns Q[i] with D[j], 'D' consumes a database residue (a gap in
+ * the query, the E direction), 'I' consumes a query residue (the F
+ * direction).  Coordinates are 0-based: the alignment covers Q[q_begin ..
+ * q_end) and D[t_begin .. t_end).  ops must hold m + n bytes.  Returns the
+ * number of operations, or -1 on invalid input or allocation failure. */
+int64_t oracle_sw_align(const uint8_t *Q, int64_t m, const uint8_t *D, int64_t n,
+                        const int8_t *SM, int32_t gap_open, int32_t gap_extend,
+                        int32_t *score, int64_t *coords, uint8_t *ops) {
+    if (m < 0 || n < 0 || gap_open < 0 || gap_extend < 0) return -1;
+    for (int64_t i = 0; i < m; ++i) if (Q[i] >= ORACLE_ALPHABET) return -1;
+    for (int64_t j = 0; j < n; ++j) if (D[j] >= ORACLE_ALPHABET) return -1;
+    *score = 0;
+    coords[0] = coords[1] = coords[2] = coords[3] = 0;
+    if (m == 0 || n == 0) return 0;
+    const int32_t Go = gap_open + gap_extend;
+    const int32_t Ge = gap_extend;
+    const int64_t W = n + 1;
+    int32_t *H = (int32_t *)calloc((size_t)((m + 1) * W), sizeof(int32_t));
+    int32_t *E = (int32_t *)calloc((size_t)((m + 1) * W), sizeof(int32_t));
+    int32_t *F = (int32_t *)calloc((size_t)((m + 1) * W), sizeof(int32_t));
+    if (!H || !E || !F) { free(H); free(E); free(F); return -1; }
+    int32_t S = 0;
+    int64_t bi = 0, bj = 0;
+    for (int64_t i = 1; i <= m; ++i) {
+        const int8_t *row = SM + (size_t)Q[i - 1] * ORACLE_ALPHABET;
+        for (int64_t j = 1; j <= n; ++j) {
+            const int64_t c = i * W + j;
+            E[c] = max2(E[c - 1] - Ge, H[c - 1] - Go);
+            F[c] = max2(F[c - W] - Ge, H[c - W] - Go);
+            int32_t h = H[c - W - 1] + row[D[j - 1]];
+            h = max2(h, E[c]);
+            h = max2(h, F[c]);
+            h = max2(h, 0);
+            H[c] = h;
+            if (h > S) { S = h; bi = i; bj = j; }
+        }
+    }
+    *score = S;
+    int64_t k = 0;  /* operations, written backwards */
+    int64_t i = bi, j = bj;
+    int state = 0;  /* 0 = H, 1 = E, 2 = F */
+    while (i > 0 && j > 0) {
+        const int64_t c = i * W + j;
+        if (state == 0) {
+            if (H[c] == 0) break;
+            if (H[c] == H[c - W - 1] + SM[(size_t)Q[i - 1] * ORACLE_ALPHABET + D[j - 1]]) {
+                ops[k++] = 'M'; --i; --j;
+            } else if (H[c] == E[c]) {
+                state = 1;
+            } else {
+                state = 2;
+            }
+        } else if (state == 1) {
+            ops[k++] = 'D';
+            state = (E[c] == H[c - 1] - Go) ? 0 : 1;
+            --j;
+        } else {
+            ops[k++] = 'I';
+            state = (F[c] == H[c - W] - Go) ? 0 : 2;
+            --i;
+        }
+    }
+    for (int64_t a = 0, b = k - 1; a < b; ++a, --b) { uint8_t t = ops[a]; ops[a] = ops[b]; ops[b] = t; }
+    coords[0] = i; coords[1] = bi; coords[2] = j; coords[3] = bj;
+    free(H); free(E); free(F);
+    return k;
 }

@@ -79,3 +79,29 @@ def literal_gotoh(q, d, sm, Go, Ge):
             F[i, j] = max(H[i - 1, j] - Go, F[i - 1, j] - Ge)
             H[i, j] = max(0, H[i - 1, j - 1] + int(sm[int(q[i - 1])][int(d[j - 1])]), E[i, j], F[i, j])
     return int(H.max())
+
+
+def alignment_score(q, d, sm, gap_open, gap_extend, q_begin, t_begin, ops):
+    """Score of an alignment given as operations (M: Q[i] with D[j]; I: Q[i]
+    against a gap; D: D[j] against a gap) starting at (q_begin, t_begin): the
+    substitution scores of the M pairs minus gap_open + k * gap_extend per
+    maximal run of k I's or k D's.  Raises if the walk leaves a sequence."""
+    i, j, total, prev = q_begin, t_begin, 0, None
+    for op in ops:
+        if op == "M":
+            total += int(sm[int(q[i]), int(d[j])])
+            i += 1
+            j += 1
+        elif op in "ID":
+            total -= gap_extend + (gap_open if op != prev else 0)
+            if op == "I":
+                i += 1
+            else:
+                j += 1
+        else:
+            raise ValueError(op)
+        if i > len(q) or j > len(d):
+            raise ValueError("alignment runs past a sequence")
+        prev = op
+    return total, i, j
+

@@ -267,3 +267,49 @@ def test_dna_brute_force(oracle_mod):
         a = rng.integers(0, 4, size=int(rng.integers(0, 6))).astype(np.uint8)
         b = rng.integers(0, 4, size=int(rng.integers(0, 6))).astype(np.uint8)
         assert oracle_mod.score(a, b, DNA_SUBMAT, 5, 2) == _pins.brute_force(a, b, DNA_SUBMAT, 5, 2)
+
+
+# --- one optimal alignment (traceback) ----------------------------------------
+
+def _check_alignment(oracle_mod, q, d, sm, go, ge):
+    s, qb, qe, tb, te, ops = oracle_mod.align(q, d, sm, go, ge)
+    assert s == oracle_mod.score(q, d, sm, go, ge)
+    total, i, j = _pins.alignment_score(q, d, sm, go, ge, qb, tb, ops)
+    assert total == s and (i, j) == (qe, te)
+    if s > 0:
+        assert ops[0] == "M" and ops[-1] == "M"  # a local alignment starts and ends on aligned pairs
+    else:
+        assert ops == "" and qb == qe and tb == te
+    return s, ops
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_alignment_reproduces_the_score(oracle_mod, seed):
+    rng = np.random.Generator(np.random.PCG64(500 + seed))
+    sm = BLOSUM62 if seed % 2 == 0 else rng.integers(-8, 9, size=(20, 20)).astype(np.int8)
+    for _ in range(20):
+        q = rng.integers(0, 20, size=int(rng.integers(0, 40))).astype(np.uint8)
+        d = rng.integers(0, 20, size=int(rng.integers(0, 40))).astype(np.uint8)
+        if rng.random() < 0.5 and len(q) > 4:
+            d = np.concatenate([d[:5], q[2:-2], d[5:]]).astype(np.uint8)  # a shared stretch
+        _check_alignment(oracle_mod, q, d, sm, int(rng.integers(0, 12)), int(rng.integers(0, 4)))
+
+
+def test_alignment_brute_force_small(oracle_mod):
+    rng = np.random.Generator(np.random.PCG64(501))
+    for _ in range(60):
+        q = rng.integers(0, 20, size=int(rng.integers(0, 6))).astype(np.uint8)
+        d = rng.integers(0, 20, size=int(rng.integers(0, 6))).astype(np.uint8)
+        s, _ = _check_alignment(oracle_mod, q, d, BLOSUM62, 3, 1)
+        assert s == _pins.brute_force(q, d, BLOSUM62, 3, 1)
+
+
+def test_alignment_of_a_gapped_copy(oracle_mod):
+    # a query and a copy with 3 extra residues in the middle: with cheap gaps
+    # the optimum bridges them with one D run of length 3
+    from workload.matrices import DNA_SUBMAT
+    rng = np.random.Generator(np.random.PCG64(502))
+    x = rng.integers(0, 4, size=80).astype(np.uint8)
+    y = np.concatenate([x[:40], rng.integers(0, 4, size=3).astype(np.uint8), x[40:]]).astype(np.uint8)
+    s, ops = _check_alignment(oracle_mod, x, y, DNA_SUBMAT, 2, 1)
+    assert s == 80 - (2 + 3 * 1) and ops.count("D") == 3 and ops.count("I") == 0
