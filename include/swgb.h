@@ -278,6 +278,53 @@ int sw_align_pair(const uint8_t *query, int64_t m, const uint8_t *target, int64_
                   int32_t gap_open, int32_t gap_extend, const sw_pair_options *opts, int32_t *score,
                   float *kernel_ms, void *stream);
 
+/*
+ * sw_traceback -- one optimal local alignment for each of a list of hits
+ * (query, database sequence) of a search, the alignment behind a score
+ * (Sec. 2.2: H[i][j] is the best score of an alignment ending at cell (i, j);
+ * the path that produced it is the alignment).  The paper's search reports
+ * scores only; this recovers the alignments of the hits a caller keeps.
+ *
+ * One warp per hit recomputes the pair's matrix in int32 and records 4 bits
+ * per cell (where H came from; whether E and F extend a gap); one thread per
+ * hit walks them back from the first cell, in row-major order, that holds the
+ * score.  Device memory: about m * n / 2 bytes per hit (held during the call).
+ *
+ *   db                    a prepared database
+ *   queries, q_offsets, n_queries   host pointers, as sw_queries_prepare
+ *   hits, n_hits          host array of (query index, database sequence index
+ *                         in the caller's order)
+ *   submat, gap_open, gap_extend    as sw_search
+ *   out                   host array of n_hits sw_alignment
+ *   ops, ops_capacity     host buffer for the operations of all hits: hit h
+ *                         gets m + n bytes at out[h].ops_offset (m, n its
+ *                         lengths); ops_capacity must be at least their sum
+ *   stream                stream for the work; the call returns when done
+ *
+ * Operations, first to last: 'M' aligns query[i] with target[j], 'I' a query
+ * residue with a gap, 'D' a target residue with a gap.  An alignment scores
+ * the substitution scores of its 'M' pairs minus gap_open + k * gap_extend per
+ * maximal run of k 'I' or k 'D'; that is out[h].score.  A score of 0 gives an
+ * empty alignment.
+ * Errors: SW_EINVAL (bad indices, small ops buffer), SW_ENOMEM, SW_ECUDA.
+ */
+typedef struct sw_hit {
+  int32_t query;   /* index into the query batch */
+  int32_t target;  /* database sequence, caller order */
+} sw_hit;
+
+typedef struct sw_alignment {
+  int32_t score;
+  int32_t q_begin, q_end;  /* the alignment covers query[q_begin, q_end) (0-based) */
+  int32_t t_begin, t_end;  /* and target[t_begin, t_end) */
+  int32_t n_ops;           /* operations at ops[ops_offset, ops_offset + n_ops) */
+  int64_t ops_offset;
+} sw_alignment;
+
+int sw_traceback(const sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int64_t n_queries,
+                 const sw_hit *hits, int64_t n_hits, const int8_t *submat, int32_t gap_open, int32_t gap_extend,
+                 sw_alignment *out, uint8_t *ops, int64_t ops_capacity, void *stream);
+
 /* Message for the last failed call on this thread ("" if none). */
 const char *sw_last_error(void);
 

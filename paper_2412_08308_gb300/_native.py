@@ -33,6 +33,7 @@ SIGNATURES = {
     "sw_queries_info": (ctypes.c_int, [_p, _pi64, _pi64, _pi64, _pi64]),
     "sw_search_noalloc": (ctypes.c_int, [_p, _p, _i64, _p, _i32, _i32, _p, _p]),
     "sw_align_pair": (ctypes.c_int, [_p, _i64, _p, _i64, _p, _i32, _i32, _p, _p, _p, _p]),
+    "sw_traceback": (ctypes.c_int, [_p, _p, _p, _i64, _p, _i64, _p, _i32, _i32, _p, _p, _i64, _p]),
     "sw_last_error": (ctypes.c_char_p, []),
 }
 
@@ -164,3 +165,27 @@ def sw_align_pair(q_ptr, m, t_ptr, n, submat_ptr, gap_open, gap_extend, opts, st
                               ctypes.byref(opts) if opts is not None else None, ctypes.byref(score),
                               ctypes.byref(ms), stream))
     return score.value, ms.value
+
+
+class SwHit(ctypes.Structure):
+    """Mirror of sw_hit (include/swgb.h)."""
+
+    _fields_ = [("query", ctypes.c_int32), ("target", ctypes.c_int32)]
+
+
+class SwAlignment(ctypes.Structure):
+    """Mirror of sw_alignment (include/swgb.h)."""
+
+    _fields_ = [("score", ctypes.c_int32), ("q_begin", ctypes.c_int32), ("q_end", ctypes.c_int32),
+                ("t_begin", ctypes.c_int32), ("t_end", ctypes.c_int32), ("n_ops", ctypes.c_int32),
+                ("ops_offset", ctypes.c_int64)]
+
+
+def sw_traceback(db, q_ptr, qoff_ptr, n_queries, hits, submat_ptr, gap_open, gap_extend, ops_buf, stream):
+    """hits: a ctypes array of SwHit; ops_buf: a writable numpy uint8 array.  Returns the SwAlignment array."""
+    out = (SwAlignment * len(hits))()
+    check(lib().sw_traceback(db, q_ptr, qoff_ptr, n_queries, hits, len(hits), submat_ptr, gap_open, gap_extend,
+                             out, ops_buf.ctypes.data_as(ctypes.c_void_p) if ops_buf.size else None, ops_buf.size,
+                             stream))
+    return out
+

@@ -45,6 +45,7 @@ class Database:
     def __init__(self, residues, offsets, stream=None):
         res, off = _seqs(residues, offsets)
         self.n = off.size - 1
+        self.lengths = np.diff(off)
         self.handle = N.sw_db_prepare(_ptr(res), _ptr(off), self.n, _stream(stream))
 
     @classmethod
@@ -174,3 +175,28 @@ def align_pair(query, target, submat, gap_open=5, gap_extend=2, opts=None, strea
     score, ms = N.sw_align_pair(_ptr(q), q.size, _ptr(t), t.size, _ptr(sm), int(gap_open), int(gap_extend), opts,
                                 _stream(stream))
     return (score, ms) if timed else score
+
+
+def traceback(db, residues, offsets, hits, submat, gap_open=10, gap_extend=2, stream=None):
+    """One optimal local alignment for each hit (query index, database index
+    in the caller's order): a list of (score, q_begin, q_end, t_begin, t_end,
+    ops) with ops a str over M (aligned pair), I (query residue against a gap)
+    and D (database residue against a gap); coordinates 0-based, ends exclusive."""
+    res, off = _seqs(residues, offsets)
+    sm = np.ascontiguousarray(submat, dtype=np.int8)
+    if sm.shape != (20, 20):
+        raise ValueError("submat must be 20x20")
+    hits = [(int(a), int(b)) for a, b in hits]
+    arr = (N.SwHit * len(hits))(*[N.SwHit(a, b) for a, b in hits])
+    qlen = np.diff(off)
+    need = sum(int(qlen[a]) if 0 <= a < qlen.size else 0 for a, _ in hits) + sum(
+        int(db.lengths[b]) if 0 <= b < len(db.lengths) else 0 for _, b in hits)
+    ops = np.zeros(max(need, 1), dtype=np.uint8)
+    out = N.sw_traceback(db.handle, _ptr(res), _ptr(off), off.size - 1, arr, _ptr(sm), int(gap_open),
+                         int(gap_extend), ops, _stream(stream))
+    result = []
+    for o in out:
+        seg = bytes(ops[o.ops_offset:o.ops_offset + o.n_ops]).decode()
+        result.append((o.score, o.q_begin, o.q_end, o.t_begin, o.t_end, seg))
+    return result
+

@@ -80,6 +80,9 @@ struct sw_db {
   int32_t max_npad = 0;
   double mean_npad = 0;
   std::vector<int32_t> h_npad;  // padded lengths in sorted order
+  std::vector<int32_t> h_len;   // true lengths in sorted order
+  std::vector<int32_t> h_pos;   // sorted position of each sequence, caller order
+  std::vector<int64_t> h_off;   // residue offsets in sorted order
 };
 
 struct sw_queries {
@@ -177,6 +180,10 @@ void free_queries(sw_queries *q) {
 namespace swgb {
 const DbView &db_view(const sw_db *db) { return db->view; }
 int db_device(const sw_db *db) { return db->device; }
+int64_t db_sorted_pos(const sw_db *db, int64_t caller_index) { return db->h_pos[caller_index]; }
+int32_t db_sorted_len(const sw_db *db, int64_t pos) { return db->h_len[pos]; }
+int32_t db_sorted_npad(const sw_db *db, int64_t pos) { return db->h_npad[pos]; }
+int64_t db_sorted_off(const sw_db *db, int64_t pos) { return db->h_off[pos]; }
 int set_last_error(int code, const char *msg) { return fail(code, "%s", msg); }
 void clear_last_error() { g_err.clear(); }
 }  // namespace swgb
@@ -220,6 +227,10 @@ int sw_db_prepare(const uint8_t *residues, const int64_t *offsets, int64_t n_seq
   }
   db->mean_npad = n_seqs ? (double)padded / n_seqs : 0;
   db->h_npad = npad;
+  db->h_len = slen;
+  db->h_off = off;
+  db->h_pos.assign(n_seqs, 0);
+  for (int64_t k = 0; k < n_seqs; ++k) db->h_pos[order[k]] = (int32_t)k;
   std::vector<uint8_t> packed((size_t)std::max<int64_t>(padded, 16), (uint8_t)kPadCode);
   for (int64_t k = 0; k < n_seqs; ++k)
     if (slen[k]) memcpy(&packed[off[k]], residues + offsets[order[k]], (size_t)slen[k]);

@@ -129,6 +129,35 @@ size_t pair_smem_bytes(int pbuf_bytes, int warps);
 int pair_max_ctas_per_sm(int R, int threads, size_t smem);
 cudaError_t launch_pair(const PairBandArgs &a, int R, int grid, int threads, size_t smem, cudaStream_t s);
 
+// Traceback of selected hits (k_trace.cu): one warp per hit fills 4-bit
+// provenance codes per cell, one thread per hit walks them back.
+struct TraceHit {
+  int64_t qoff;       // query residues in qres
+  int64_t toff;       // target residues in tres (the database's sorted, padded residues)
+  int64_t dir_off;    // bytes into dirs: mrow * npad / 2, column-major nibbles (row i of column j at j * mrow + i)
+  int64_t strip_off;  // uint2 entries into strips: npad (chunk boundary rows)
+  int64_t ops_off;    // bytes into ops: m + n
+  int32_t m, n, npad, mrow;  // query and target lengths, padded target length, rows padded to whole chunks
+};
+struct TraceResult {
+  int32_t score, end_i, end_j;  // best score and its cell (1-based row, column; first in row-major order)
+  int32_t begin_i, begin_j;     // the alignment covers rows begin_i+1 .. end_i, columns begin_j+1 .. end_j
+  int32_t n_ops;
+};
+struct TraceArgs {
+  const uint8_t *qres, *tres;
+  const int8_t *submat;  // 20x20
+  const TraceHit *hits;
+  int32_t nhits;
+  uint8_t *dirs;
+  uint2 *strips;
+  uint8_t *ops;
+  TraceResult *results;
+  Scoring sc;
+};
+int trace_rows_per_chunk();
+cudaError_t launch_trace(const TraceArgs &a, cudaStream_t s);
+
 // launchers (k_inter.cu)
 int inter_threads();
 int inter_chains_per_cta(int L);
@@ -165,6 +194,10 @@ cudaError_t launch_rescue_tasks(const int32_t *flag_count, const QDesc *qd, int3
 // Accessors for translation units other than api.cu (the sw_db layout is private to it).
 const DbView &db_view(const struct ::sw_db *db);
 int db_device(const struct ::sw_db *db);
+int64_t db_sorted_pos(const struct ::sw_db *db, int64_t caller_index);  // caller order -> sorted position
+int32_t db_sorted_len(const struct ::sw_db *db, int64_t pos);           // true length at a sorted position
+int32_t db_sorted_npad(const struct ::sw_db *db, int64_t pos);          // padded length at a sorted position
+int64_t db_sorted_off(const struct ::sw_db *db, int64_t pos);           // residue offset at a sorted position
 // Record the thread's last error message (see sw_last_error) and return `code`.
 int set_last_error(int code, const char *msg);
 void clear_last_error();
