@@ -105,13 +105,11 @@ extern "C" int sw_align_pair(const uint8_t *query, int64_t m, const uint8_t *tar
 
   // geometry: bands of 32 * R query rows, one warp each; each warp stages its
   // band's profile (21 residue rows) in shared memory
-  // Bands in flight are the parallelism: one warp each.  Rows per lane 16
-  // once the pair has 8 bands per SM at that height, else 8 (4 bands per SM),
-  // else 4, trading work per step for bands; the warps of a CTA are the
-  // bands per SM, so that every SM gets bands.
-  auto bands_of = [&](int r) { return (m + 32 * (int64_t)r - 1) / (32 * (int64_t)r); };
-  int R = o.rows_per_lane;
-  if (!R) R = bands_of(16) >= 8 * (int64_t)sms ? 16 : bands_of(8) >= 4 * (int64_t)sms ? 8 : 4;
+  // Bands in flight are the parallelism, one warp each; the warps of a CTA are
+  // the bands per SM, so that every SM gets bands.  Rows per lane 16: on
+  // pairs with few bands per SM, 8 or 4 (more, shorter bands) measured slower
+  // (the ramp of the band pipeline grows with the band count), and 24 spills.
+  const int R = o.rows_per_lane ? o.rows_per_lane : 16;
   const int64_t B = 32 * (int64_t)R;
   const int64_t nbands64 = (m + B - 1) / B;
   if (nbands64 >= ((int64_t)1 << 31)) return pair_fail(SW_EINVAL, "sw_align_pair: too many bands");
