@@ -124,7 +124,6 @@ struct PairBandArgs {
   int32_t *status;         // SW_ETIMEOUT on an expired wait
   Scoring sc;
 };
-int pair_threads();
 size_t pair_smem_bytes(int pbuf_bytes, int warps);
 int pair_max_ctas_per_sm(int R, int threads, size_t smem);
 cudaError_t launch_pair(const PairBandArgs &a, int R, int grid, int threads, size_t smem, cudaStream_t s);
@@ -160,7 +159,6 @@ cudaError_t launch_trace(const TraceArgs &a, cudaStream_t s);
 
 // launchers (k_inter.cu)
 int inter_threads();
-int inter_chains_per_cta(int L);
 bool inter_supported_R(int R);
 size_t inter_smem_bytes(int pbuf_bytes, int pbuf_count, int threads);
 cudaError_t launch_inter(const InterArgs &a, int R, int form, int grid, int threads, size_t smem,

@@ -426,8 +426,6 @@ cudaError_t launch_pair_one(const PairBandArgs &a, int grid, int threads, size_t
 
 int inter_threads() { return kThreads; }
 
-int pair_threads() { return kPairThreads; }
-
 size_t pair_smem_bytes(int pbuf_bytes, int warps) { return (size_t)warps * (pbuf_bytes + kRingBytes); }
 
 int pair_max_ctas_per_sm(int R, int threads, size_t smem) {
@@ -445,9 +443,6 @@ cudaError_t launch_pair(const PairBandArgs &a, int R, int grid, int threads, siz
   if (R == 24) return launch_pair_one<24>(a, grid, threads, smem, s);
   return cudaErrorInvalidValue;
 }
-int inter_chains_per_cta(int L) { return (kThreads / 32) * (32 / L); }
-int inter_ring_bytes() { return kRingBytes; }
-int inter_chains_per_warp_slots() { return kChainsPerWarpMax; }
 
 size_t inter_smem_bytes(int pbuf_bytes, int pbuf_count, int threads) {
   return 128 + (size_t)pbuf_count * pbuf_bytes + (size_t)(threads / 32) * kChainsPerWarpMax * kRingBytes;
