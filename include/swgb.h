@@ -242,8 +242,10 @@ int sw_search_noalloc(const sw_db *db, const uint8_t *query, int64_t m, const in
  * a warp is a chain of 32 lanes that sweeps the band across the whole target,
  * and band b starts on a column as soon as band b-1 has finished it, so the
  * bands run as a pipeline over every warp of every SM (a cooperative launch;
- * every wait between warps is bounded).  Cells are int32, so scores up to
- * 2^31 - 1 are exact (a million-residue identity scores 10^6 with +1 matches).
+ * every wait between warps is bounded).  Cells are int32 (a million-residue
+ * identity scores 10^6 with +1 matches); the bottom rows passed between bands
+ * keep H and F + Go in 31 bits, so the call requires
+ * max(SM) * min(m, n) + gap_open + gap_extend < 2^31.
  *
  *   query, m     host pointer to m residue codes 0..19 (DNA: any 4 or 5 of
  *                them, e.g. A C G T N = 0 1 2 3 4), m < 2^31
@@ -256,10 +258,10 @@ int sw_search_noalloc(const sw_db *db, const uint8_t *query, int64_t m, const in
  *   score        host pointer, receives S = max(0, max H)
  *   kernel_ms    host pointer or NULL: duration of the band kernel
  *   stream       stream for the work (NULL = legacy default); the call
- *                allocates its device scratch (the boundary rows of the bands
- *                in flight, at most a quarter of the free memory or 8 GB, the
- *                query profile, the target), returns when the score is in
- *                *score and frees the scratch
+ *                allocates its device scratch (a ring of boundary rows per
+ *                band in flight, 8 bytes per column, 8,192 columns by
+ *                default; the query profile; the target), returns when the
+ *                score is in *score and frees the scratch
  *
  * Errors: SW_EINVAL, SW_ENOMEM, SW_ECUDA, SW_ETIMEOUT.
  */

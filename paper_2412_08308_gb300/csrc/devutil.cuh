@@ -81,6 +81,18 @@ __device__ __forceinline__ void st_release(int32_t *p, int32_t v) {
   asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Relaxed 64-bit accesses at gpu scope: single-copy atomic, served by L2 (never
+// a stale L1 line), no ordering against other accesses.
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p));
+  return v;
+}
+
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v));
+}
+
 // A wait on another warp of a long pipeline, which may legitimately last as
 // long as a whole band takes: ~60 s at GB300 clocks.
 constexpr long long kLongWaitBudgetCycles = 120000000000LL;

@@ -108,7 +108,7 @@ struct InterArgs {
   int32_t *status;          // device status word (SW_ETIMEOUT on an expired wait)
 };
 
-// Arguments of the pair-band kernel (k_inter.cu): one long pair, int32 cells,
+// Arguments of the pair-band kernel (k_pair.cu): one long pair, int32 cells,
 // one band of 32 * R query rows per warp.
 struct PairBandArgs {
   const uint8_t *target;   // target codes padded with the pad code to npad (a multiple of 16)
@@ -116,10 +116,11 @@ struct PairBandArgs {
   int32_t nbands;
   const uint8_t *prof;     // nbands profile chunks of band_bytes = rows * stride (L = 32)
   int32_t band_bytes, stride, pbuf_bytes;
-  uint2 *strips;           // [nslots][window] rings of bottom rows (H, F)
+  unsigned long long *strips;  // [nslots][window] rings of tagged bottom-row entries, zeroed before launch
   int32_t nslots;          // >= (warps of the grid) + 1, or nbands
-  int32_t window;          // columns per ring (a multiple of 16)
-  int32_t *prog, *cons;    // [nbands] columns published / consumed, zeroed before launch
+  int32_t window;          // columns per ring (a multiple of 16, >= 256)
+  int32_t cons_every;      // blocks of 16 columns between hand-backs of consumed columns
+  int32_t *cons;           // [nbands] columns consumed by the band below, zeroed before launch
   int32_t *best;           // max over all cells (atomicMax), zeroed before launch
   int32_t *status;         // SW_ETIMEOUT on an expired wait
   Scoring sc;

@@ -25,12 +25,14 @@
 // Cell arithmetic
 // ---------------
 // int32 form: the twelve-instruction body of Algorithm 1, one cell per lane op.
-// packed form: two cells per 32-bit word, each 16-bit half holding the true
-// value plus a bias B (B >= Go + Ge + K) so every intermediate stays in
-// [0, 32767]; additions are plain 32-bit IADD/IADD3 (no carry or borrow can
-// cross the halves) and maxima are full-rate per-half VIMNMX (__vmaxs2).  A
-// half whose final stored score exceeds 32767 - max(SM) may have overflowed;
-// it is flagged and recomputed exactly in int32 (rescue pass).
+// packed forms: two cells per 32-bit word, each 16-bit half a signed cell
+// value (two database sequences, or two queries against one sequence);
+// additions are per-half (__vadd2 / __vsub2, no carry crosses the halves) and
+// maxima are per-half VIMNMX (__vmaxs2, __vimax_s16x2_relu for the zero floor).
+// E and F never fall below -Go, so no half wraps downward; a half whose final
+// score exceeds 32767 - max(SM) may have wrapped upward and is flagged and
+// recomputed exactly in int32 (rescue pass; query pairs are planned only where
+// no half can pass that bound, and a half that does sets an error status).
 #include "devutil.cuh"
 #include "dp_common.cuh"
 #include "internal.h"
@@ -40,40 +42,20 @@ namespace swgb {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kPairThreads = 512;  // pair-band kernel: 16 warps, one band each
-constexpr int kCrossBatch = 4;     // pair-band kernel: blocks per published count (rings >= 16 blocks)
 constexpr int kChainsPerWarpMax = 8;  // lanes per chain >= 4
 constexpr int kRingBytes = 320;       // residues: 2 slots x 2 seqs x 16 B; boundary: 2 slots x 16 x 8 B
-
-// Boundary strips between chains of different warps (the pair-band kernel):
-// the strip of the band above is read once its producer has published the
-// columns (prog_in), and the columns read are handed back (cons_in) so the
-// producer may reuse them; strips are rings of `window` columns.
-struct CrossIO {
-  const uint2 *in;
-  uint2 *out;
-  const int32_t *prog_in;
-  int32_t *cons_in;
-  const int32_t *cons_out;
-  int32_t *prog_out;
-  int32_t window;
-  int32_t *status;
-};
 
 // One pass of a chain over all columns of its unit for the rows of one chunk.
 // restart (16-bit forms): halves whose rows start a new query in this chunk;
 // they take the matrix top boundary instead of the strip of the chunk above.
-// CROSS: the strips are another warp's (see CrossIO); returns false when a
-// wait on that warp expired.
-template <int R, int FORM, bool CROSS = false>
-__device__ __forceinline__ bool chain_pass(const uint8_t *__restrict__ pch, const int stride, const int L,
+template <int R, int FORM>
+__device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, const int stride, const int L,
                                            const int k, const int lane, const int slot, const int gstride,
                                            const bool live, const int nblk,
                                            const int npad, const int npa, const int npb,
                                            const uint8_t *__restrict__ resA, const uint8_t *__restrict__ resB,
                                            uint8_t *ring, uint2 *gb, const bool prev, const bool next,
-                                           const uint32_t restart, const Consts &cs, Word<FORM> &S,
-                                           const CrossIO &x = CrossIO{}) {
+                                           const uint32_t restart, const Consts &cs, Word<FORM> &S) {
   using W = Word<FORM>;
   constexpr bool PACKED = FORM != kFormInt32;      // 16-bit halves
   constexpr bool PAIRS = FORM == kFormPacked;      // two database sequences per unit
@@ -86,11 +68,6 @@ __device__ __forceinline__ bool chain_pass(const uint8_t *__restrict__ pch, cons
   const int src = (k > 0) ? lane - 1 : lane;
   const bool lead = live && k == 0;
   const bool tail = live && (k == L - 1) && next;
-  bool failed = false;
-  // CROSS: the other warps' counters as last read (polled again only when they
-  // fall short) and this chain's pending publications, released every
-  // kCrossBatch blocks (a release waits for this thread's earlier accesses)
-  int seen_prog = 0, seen_cons = 0, copied = 0;
   uint8_t *rres = ring;                                  // [slot][seq][16 B]
   uint2 *rgb = reinterpret_cast<uint2 *>(ring + 64);     // [slot][16]
   // this lane's profile slot: R bytes, or (query pairs) R/4 16-byte groups gstride apart
@@ -107,28 +84,8 @@ __device__ __forceinline__ bool chain_pass(const uint8_t *__restrict__ pch, cons
       else *reinterpret_cast<uint4 *>(d + 16) = make_uint4(0x14141414u, 0x14141414u, 0x14141414u, 0x14141414u);
     }
     if (prev && col < npad) {
-      if constexpr (CROSS) {
-        const int need = min(col + kColBlock, npad);
-        if (!failed && seen_prog < need) {
-          seen_prog = wait_flag_value(x.prog_in, need, kLongWaitBudgetCycles);
-          if (seen_prog < need) {
-            failed = true;
-            atomicExch(x.status, SW_ETIMEOUT);
-          }
-        }
-        if (!failed) {
-          const uint4 *src = reinterpret_cast<const uint4 *>(x.in + col % x.window);
-          uint4 *dst = reinterpret_cast<uint4 *>(rgb + slot * 16);
 #pragma unroll
-          for (int i = 0; i < 8; ++i) dst[i] = __ldcg(src + i);
-          copied = need;
-          // copied: the producer may reuse these columns
-          if (blk % kCrossBatch == kCrossBatch - 1 || need == npad) st_release(x.cons_in, copied);
-        }
-      } else {
-#pragma unroll
-        for (int i = 0; i < 8; ++i) cp_async16(rgb + slot * 16 + 2 * i, gb + col + 2 * i);
-      }
+      for (int i = 0; i < 8; ++i) cp_async16(rgb + slot * 16 + 2 * i, gb + col + 2 * i);
     }
     cp_async_commit();
   };
@@ -143,19 +100,6 @@ __device__ __forceinline__ bool chain_pass(const uint8_t *__restrict__ pch, cons
     // lane 0's columns of this block are all real or all padding (npad is a multiple of 16)
     const bool real = blk * kColBlock < npad;
     const bool from_strip = prev && real;
-    if (CROSS && tail && !failed) {
-      // room in the consumer's ring for the columns this block writes
-      const int jmax = min(blk * kColBlock + kColBlock - 1 - (L - 1), npad - 1);  // last column written
-      const int need = jmax + 1 - x.window;
-      if (jmax >= 0 && seen_cons < need) {
-        seen_cons = wait_flag_value(x.cons_out, need, kLongWaitBudgetCycles);
-        if (seen_cons < need) {
-          failed = true;
-          atomicExch(x.status, SW_ETIMEOUT);
-        }
-      }
-    }
-    if (CROSS && __any_sync(0xffffffffu, failed)) break;
     if (lead) {
       cp_async_wait<1>();
       ra4 = *reinterpret_cast<const uint4 *>(rres + (blk & 1) * 32);
@@ -196,22 +140,16 @@ __device__ __forceinline__ bool chain_pass(const uint8_t *__restrict__ pch, cons
         outRes = inRes;
         if (tail) {
           const int j = t - (L - 1);
-          if (j >= 0 && j < npad) {
-            if constexpr (CROSS) x.out[j % x.window] = make_uint2((uint32_t)outH, (uint32_t)outF);
-            else gb[j] = make_uint2((uint32_t)outH, (uint32_t)outF);
-          }
+          if (j >= 0 && j < npad) gb[j] = make_uint2((uint32_t)outH, (uint32_t)outF);
         }
       }
     }
-    if (CROSS && tail && (blk % kCrossBatch == kCrossBatch - 1 || blk == nblk - 1))  // publish the columns written
-      st_release(x.prog_out, min(max(0, (blk + 1) * kColBlock - (L - 1)), npad));
     if (lead) {
       if (blk + 2 < nblk) prefetch(blk + 2);
       else cp_async_commit();
     }
   }
   if (lead) cp_async_wait<0>();
-  return !__any_sync(0xffffffffu, failed);
 }
 
 template <int R, int FORM>
@@ -333,50 +271,6 @@ __global__ void __launch_bounds__(kThreads, 2) inter_kernel(const InterArgs a) {
   }
 }
 
-// Warp bands over one long (query, target) pair, int32 cells (the pairwise
-// alignment of two long sequences, Sec. 2.2 case (a); Fig. 1 intra-sequence
-// parallelism).  Band b is query rows [32 R b, 32 R (b+1)): one warp is a
-// chain of 32 lanes of R rows (the inter-task chain) that sweeps every target
-// column.  Warp w of the grid takes bands w, w + warps, ... in order; a band's
-// top boundary is the bottom row of the band above, read from that band's
-// strip as soon as its warp has published the columns, so the bands run as a
-// pipeline over every warp of every SM.  All warps are resident (cooperative
-// launch), a band waits only on the band above (data) and the band below
-// (room in the strip ring), and every wait is bounded.
-template <int R>
-__global__ void __launch_bounds__(kPairThreads, 1) pair_band_kernel(const PairBandArgs a) {
-  using W = Word<kFormInt32>;
-  extern __shared__ __align__(128) uint8_t smem[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nw = blockDim.x >> 5;
-  uint8_t *pbuf = smem + (size_t)warp * (a.pbuf_bytes + kRingBytes);
-  uint8_t *ring = pbuf + a.pbuf_bytes;
-  const Consts cs = make_consts(a.sc);
-  const int nblk = (a.npad + 31 + kColBlock - 1) / kColBlock;
-  W S = (W)0;
-  for (int b = blockIdx.x * nw + warp; b < a.nbands; b += gridDim.x * nw) {
-    const uint4 *src = reinterpret_cast<const uint4 *>(a.prof + (int64_t)b * a.band_bytes);
-    for (int i = lane; i < a.band_bytes / 16; i += 32) reinterpret_cast<uint4 *>(pbuf)[i] = __ldg(src + i);
-    __syncwarp();
-    CrossIO x;
-    x.in = a.strips + (size_t)((b + a.nslots - 1) % a.nslots) * a.window;
-    x.out = a.strips + (size_t)(b % a.nslots) * a.window;
-    x.prog_in = a.prog + (b > 0 ? b - 1 : 0);
-    x.cons_in = a.cons + (b > 0 ? b - 1 : 0);
-    x.cons_out = a.cons + b;
-    x.prog_out = a.prog + b;
-    x.window = a.window;
-    x.status = a.status;
-    const bool ok = chain_pass<R, kFormInt32, true>(pbuf, a.stride, 32, lane, lane, lane, 0, true, nblk, a.npad,
-                                                    a.npad, 0, a.target, a.target, ring, nullptr, b > 0,
-                                                    b + 1 < a.nbands, 0u, cs, S, x);
-    __syncwarp();
-    if (!ok) break;
-  }
-  for (int d = 16; d > 0; d >>= 1) S = max(S, (W)__shfl_xor_sync(0xffffffffu, S, d));
-  if (lane == 0) atomicMax(a.best, S);
-}
-
 template <int R, int FORM>
 cudaError_t launch_one(const InterArgs &a, int grid, int threads, size_t smem, cudaStream_t s) {
   inter_kernel<R, FORM><<<grid, threads, smem, s>>>(a);
@@ -401,48 +295,9 @@ int configure_one(int threads, size_t smem) {
   return n;
 }
 
-template <int R>
-int configure_pair_one(int threads, size_t smem) {
-  auto kern = pair_band_kernel<R>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  return n;
-}
-
-template <int R>
-cudaError_t launch_pair_one(const PairBandArgs &a, int grid, int threads, size_t smem, cudaStream_t s) {
-  void *args[] = {(void *)&a};
-  return cudaLaunchCooperativeKernel((const void *)pair_band_kernel<R>, dim3(grid), dim3(threads), args, smem, s);
-}
-
 }  // namespace
 
 int inter_threads() { return kThreads; }
-
-size_t pair_smem_bytes(int pbuf_bytes, int warps) { return (size_t)warps * (pbuf_bytes + kRingBytes); }
-
-int pair_max_ctas_per_sm(int R, int threads, size_t smem) {
-  if (R == 4) return configure_pair_one<4>(threads, smem);
-  if (R == 8) return configure_pair_one<8>(threads, smem);
-  if (R == 16) return configure_pair_one<16>(threads, smem);
-  if (R == 24) return configure_pair_one<24>(threads, smem);
-  return 0;
-}
-
-cudaError_t launch_pair(const PairBandArgs &a, int R, int grid, int threads, size_t smem, cudaStream_t s) {
-  if (R == 4) return launch_pair_one<4>(a, grid, threads, smem, s);
-  if (R == 8) return launch_pair_one<8>(a, grid, threads, smem, s);
-  if (R == 16) return launch_pair_one<16>(a, grid, threads, smem, s);
-  if (R == 24) return launch_pair_one<24>(a, grid, threads, smem, s);
-  return cudaErrorInvalidValue;
-}
 
 size_t inter_smem_bytes(int pbuf_bytes, int pbuf_count, int threads) {
   return 128 + (size_t)pbuf_count * pbuf_bytes + (size_t)(threads / 32) * kChainsPerWarpMax * kRingBytes;

@@ -1,5 +1,5 @@
 // sw_align_pair: the score of one long (query, target) pair, computed by the
-// pair-band kernel (k_inter.cu) as a pipeline of query-row bands, one per
+// pair-band kernel (k_pair.cu) as a pipeline of query-row bands, one per
 // warp, across every warp of every SM.
 #include <algorithm>
 #include <cstdio>
@@ -96,6 +96,11 @@ extern "C" int sw_align_pair(const uint8_t *query, int64_t m, const uint8_t *tar
                      o.rows_per_lane);
   if (o.max_ctas < 0) return pair_fail(SW_EINVAL, "sw_align_pair: negative max_ctas");
   if (m == 0 || n == 0) return SW_OK;
+  // H <= max(SM) * min(m, n); the boundary entries between bands keep H and
+  // F + Go in 31 bits each
+  if ((int64_t)std::max(0, smax) * std::min(m, n) + (int64_t)gap_open + gap_extend >= ((int64_t)1 << 31))
+    return pair_fail(SW_EINVAL, "sw_align_pair: scores could pass 2^31 - 1 - Go (max(SM) %lld x %lld residues)",
+                     smax, std::min(m, n));
 
   cudaStream_t s = (cudaStream_t)stream;
   int dev = 0, sms = 1;
@@ -135,26 +140,25 @@ extern "C" int sw_align_pair(const uint8_t *query, int64_t m, const uint8_t *tar
   const int64_t gw = grid * warps;
   const int64_t nslots = std::min<int64_t>(nbands64, gw + 1);
 
-  // strip rings: whole rows when they fit a quarter of the free memory (up to
-  // 8 GB), else rings of fewer columns; a band then runs at most that many
-  // columns ahead of the band below it.  The band below may still be queued
-  // behind a band of the same round on its warp, so the first band of a
-  // round must be able to finish while each band of the round holds a full
-  // ring: rings of at least npad / (warps of the grid) columns.
+  // boundary rings: a band runs at most `window` columns ahead of the band
+  // below it, which hands consumed columns back every cons_every blocks (at
+  // most an eighth of the ring).  The band below may still be queued behind a
+  // band of the same round on its warp, so the first band of a round must be
+  // able to finish while each band of the round holds a full ring: rings of
+  // at least npad / (warps of the grid) columns, plus the hand-back interval
+  // and the lead of a band over the one below.  8,192 columns by default.
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = (size_t)1 << 30;
-  const int64_t budget = std::min<int64_t>((int64_t)free_b / 4, (int64_t)8 << 30);
-  int64_t window = std::min<int64_t>(npad, budget / std::max<int64_t>(1, nslots * (int64_t)sizeof(uint2)));
-  window = std::max<int64_t>(4096, window / kColBlock * kColBlock);
-  if (o.ring_columns) window = o.ring_columns;
-  window = std::max<int64_t>(window, round_up((npad + gw - 1) / gw + 64, kColBlock));
+  int64_t window = o.ring_columns ? o.ring_columns : 8192;
+  window = std::max<int64_t>(window, round_up(((npad + gw - 1) / gw + 64) * 8 / 7 + 1, kColBlock));
   window = std::min<int64_t>(window, npad);
+  const int cons_every = (int)std::max<int64_t>(1, std::min<int64_t>(16, window / kColBlock / 8));
 
   // device scratch: query, target, matrix, plan, profile, strips, progress, result words
   const size_t b_q = round_up(m, 256), b_t = round_up(npad, 256), b_sub = 512, b_qd = 256;
   const size_t b_prof = round_up(nbands64 * (int64_t)qd.chunk_bytes, 256);
-  const size_t b_strip = round_up(nslots * window * (int64_t)sizeof(uint2), 256);
-  const size_t b_prog = round_up(8 * nbands64, 256), b_words = 256;
+  const size_t b_strip = round_up(nslots * window * (int64_t)sizeof(unsigned long long), 256);
+  const size_t b_prog = round_up(4 * nbands64, 256), b_words = 256;
   const size_t bytes = b_q + b_t + b_sub + b_qd + b_prof + b_strip + b_prog + b_words;
   if (bytes > free_b)
     return pair_fail(SW_ENOMEM, "sw_align_pair: needs %lld bytes of device memory, %lld free", (long long)bytes,
@@ -172,8 +176,8 @@ extern "C" int sw_align_pair(const uint8_t *query, int64_t m, const uint8_t *tar
   int8_t *d_sub = (int8_t *)(d_t + b_t);
   QDesc *d_qd = (QDesc *)((uint8_t *)d_sub + b_sub);
   uint8_t *d_prof = (uint8_t *)d_qd + b_qd;
-  uint2 *d_strip = (uint2 *)(d_prof + b_prof);
-  int32_t *d_prog = (int32_t *)((uint8_t *)d_strip + b_strip);  // [nbands] published, then [nbands] consumed
+  unsigned long long *d_strip = (unsigned long long *)(d_prof + b_prof);
+  int32_t *d_prog = (int32_t *)((uint8_t *)d_strip + b_strip);  // [nbands] columns consumed
   int32_t *d_words = (int32_t *)((uint8_t *)d_prog + b_prog);  // [0] best, [1] status
 
   std::vector<uint8_t> tpad((size_t)npad, (uint8_t)kPadCode);
@@ -182,7 +186,7 @@ extern "C" int sw_align_pair(const uint8_t *query, int64_t m, const uint8_t *tar
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_t, tpad.data(), (size_t)npad, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_sub, submat, 400, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_qd, &qd, sizeof qd, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d_prog, 0, b_prog + b_words, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_strip, 0, b_strip + b_prog + b_words, s);
   if (e != cudaSuccess) return pair_cuda(e, "upload");
 
   Scoring scr{};
@@ -205,8 +209,8 @@ extern "C" int sw_align_pair(const uint8_t *query, int64_t m, const uint8_t *tar
   a.strips = d_strip;
   a.nslots = (int32_t)nslots;
   a.window = (int32_t)window;
-  a.prog = d_prog;
-  a.cons = d_prog + nbands64;
+  a.cons_every = cons_every;
+  a.cons = d_prog;
   a.best = d_words;
   a.status = d_words + 1;
   a.sc = scr;
