@@ -268,7 +268,8 @@ int sw_search_noalloc(const sw_db *db, const uint8_t *query, int64_t m, const in
 typedef struct sw_pair_options {
   int32_t band_warps;     /* at most this many warps (bands in flight) per CTA, 1..16; 0 = enough
                              to give every SM bands, at most 16 */
-  int32_t rows_per_lane;  /* 4, 8, 16 or 24 (a band is 32 x rows_per_lane query rows); 0 = 16 */
+  int32_t rows_per_lane;  /* 4, 8, 16 or 24 (a band is 32 x rows_per_lane query rows); 0 = 16, or 8
+                             when 512-row bands would give fewer than 3 per SM */
   int32_t max_ctas;       /* at most this many CTAs; 0 = all that fit */
   int32_t ring_columns;   /* columns each band's boundary ring holds, a multiple of 16 >= 256 (a band
                              runs at most that far ahead of the band below); 0 = automatic */

@@ -3,9 +3,10 @@
 // parallelism).  Band b is query rows [32 R b, 32 R (b+1)): one warp is a
 // chain of 32 lanes of R rows (the inter-task chain of k_inter.cu) that sweeps
 // every target column.  Warp w of the grid takes bands w, w + warps, ... in
-// order; a band's top boundary is the bottom row of the band above, read from
-// that band's ring as soon as the entries are there, so the bands run as a
-// pipeline over every warp of every SM.  All warps are resident (cooperative
+// order (warps numbered across the SMs first, so that even a few bands per SM
+// land on every SM); a band's top boundary is the bottom row of the band
+// above, read from that band's ring as soon as the entries are there, so the
+// bands run as a pipeline over every warp of every SM.  All warps are resident (cooperative
 // launch), a band waits only on the band above (data) and on the band below
 // (room in its ring), and every wait is bounded.
 //
@@ -232,7 +233,8 @@ __global__ void __launch_bounds__(kPairThreads, 1) pair_band_kernel(const PairBa
   const Consts cs = make_consts(a.sc);
   const int nblk = (a.npad + 31 + kColBlock - 1) / kColBlock;
   int32_t S = 0;
-  for (int b = blockIdx.x * nw + warp; b < a.nbands; b += gridDim.x * nw) {
+  // global warp g = warp * grid + CTA: bands spread over the SMs first
+  for (int b = warp * gridDim.x + blockIdx.x; b < a.nbands; b += gridDim.x * nw) {
     const uint4 *src = reinterpret_cast<const uint4 *>(a.prof + (int64_t)b * a.band_bytes);
     for (int i = lane; i < a.band_bytes / 16; i += 32) reinterpret_cast<uint4 *>(pbuf)[i] = __ldg(src + i);
     __syncwarp();

@@ -111,10 +111,12 @@ extern "C" int sw_align_pair(const uint8_t *query, int64_t m, const uint8_t *tar
   // geometry: bands of 32 * R query rows, one warp each; each warp stages its
   // band's profile (21 residue rows) in shared memory
   // Bands in flight are the parallelism, one warp each; the warps of a CTA are
-  // the bands per SM, so that every SM gets bands.  Rows per lane 16: on
-  // pairs with few bands per SM, 8 or 4 (more, shorter bands) measured slower
-  // (the ramp of the band pipeline grows with the band count), and 24 spills.
-  const int R = o.rows_per_lane ? o.rows_per_lane : 16;
+  // the bands per SM, so that every SM gets bands.  Rows per lane 16, or 8
+  // when that leaves fewer than 3 bands per SM (more, shorter bands fill the
+  // SMs better there, while elsewhere the longer ramp of the band pipeline
+  // and the per-column overhead of shorter bands cost more; 4 and 24 rows
+  // measured slower on every pair).
+  const int R = o.rows_per_lane ? o.rows_per_lane : ((m + 511) / 512 < 3 * (int64_t)sms ? 8 : 16);
   const int64_t B = 32 * (int64_t)R;
   const int64_t nbands64 = (m + B - 1) / B;
   if (nbands64 >= ((int64_t)1 << 31)) return pair_fail(SW_EINVAL, "sw_align_pair: too many bands");
@@ -135,7 +137,9 @@ extern "C" int sw_align_pair(const uint8_t *query, int64_t m, const uint8_t *tar
   if (smem > 200 * 1024) return pair_fail(SW_EINVAL, "sw_align_pair: band profile too large for shared memory");
   const int occ = pair_max_ctas_per_sm(R, threads, smem);
   if (occ <= 0) return pair_fail(SW_ECUDA, "sw_align_pair: cannot configure the pair kernel");
-  int64_t grid = std::min<int64_t>((nbands64 + warps - 1) / warps, (int64_t)sms * occ);
+  // every SM gets a CTA (the kernel deals bands to the SMs in turn)
+  int64_t grid = std::min<int64_t>(std::max<int64_t>((nbands64 + warps - 1) / warps, std::min<int64_t>(sms, nbands64)),
+                                   (int64_t)sms * occ);
   if (o.max_ctas) grid = std::min<int64_t>(grid, o.max_ctas);
   const int64_t gw = grid * warps;
   const int64_t nslots = std::min<int64_t>(nbands64, gw + 1);

@@ -114,3 +114,16 @@ def test_invalid_arguments(api):
         with pytest.raises(SwError) as e:
             call()
         assert e.value.code == SW_EINVAL
+
+
+def test_score_bound(api):
+    # scores must stay below 2^31 - Go: max(SM) = 63 and 35M residues could
+    # reach 63 x 35M > 2^31, refused before any device work
+    from paper_2412_08308_gb300._native import SW_EINVAL, SwError
+
+    sm = np.full((20, 20), -3, dtype=np.int8)
+    np.fill_diagonal(sm, 63)
+    x = np.zeros(35_000_000, dtype=np.uint8)
+    with pytest.raises(SwError) as e:
+        api.align_pair(x, x, sm, 5, 2)
+    assert e.value.code == SW_EINVAL
