@@ -259,7 +259,7 @@ int sw_search_noalloc(const sw_db *db, const uint8_t *query, int64_t m, const in
  *   kernel_ms    host pointer or NULL: duration of the band kernel
  *   stream       stream for the work (NULL = legacy default); the call
  *                allocates its device scratch (a ring of boundary rows per
- *                band in flight, 8 bytes per column, 8,192 columns by
+ *                band in flight, 8 bytes per column, 32,768 columns by
  *                default; the query profile; the target), returns when the
  *                score is in *score and frees the scratch
  *

@@ -150,10 +150,13 @@ extern "C" int sw_align_pair(const uint8_t *query, int64_t m, const uint8_t *tar
   // band of the same round on its warp, so the first band of a round must be
   // able to finish while each band of the round holds a full ring: rings of
   // at least npad / (warps of the grid) columns, plus the hand-back interval
-  // and the lead of a band over the one below.  8,192 columns by default.
+  // and the lead of a band over the one below.  32,768 columns by default:
+  // shorter rings stall the last bands of a round while the band below waits
+  // for its warp (7M x 5M: 2,447 GCUPS at 8,192, 2,485 from 16,384 up; 3M x
+  // 3M: 2,281 and 2,325 from 32,768 up).
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = (size_t)1 << 30;
-  int64_t window = o.ring_columns ? o.ring_columns : 8192;
+  int64_t window = o.ring_columns ? o.ring_columns : 32768;
   window = std::max<int64_t>(window, round_up(((npad + gw - 1) / gw + 64) * 8 / 7 + 1, kColBlock));
   window = std::min<int64_t>(window, npad);
   const int cons_every = (int)std::max<int64_t>(1, std::min<int64_t>(16, window / kColBlock / 8));
