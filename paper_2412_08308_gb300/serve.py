@@ -52,10 +52,14 @@ class Server:
     max_batch   most queries admitted into one batch
     n_streams   batches in flight at once (one CUDA stream each)
     mem_budget  device bytes the in-flight batches may hold (scores, scratch)
+    policy      "fifo" admits requests in arrival order; "sjf" admits the
+                shortest queries first (their cells, query length x database,
+                are the service time), except that a request waiting at least
+                age_s seconds goes ahead of every younger one, oldest first
     """
 
     def __init__(self, db, submat, gap_open=10, gap_extend=2, mode="packed", max_batch=2, n_streams=2,
-                 mem_budget=8 << 30, opts=None):
+                 mem_budget=8 << 30, opts=None, policy="sjf", age_s=1.0):
         import torch
 
         self.torch = torch
@@ -64,6 +68,10 @@ class Server:
         self.gap_open, self.gap_extend, self.mode = int(gap_open), int(gap_extend), _mode(mode)
         self.max_batch = int(max_batch)
         self.mem_budget = int(mem_budget)
+        if policy not in ("fifo", "sjf"):
+            raise ValueError("policy must be 'fifo' or 'sjf'")
+        self.policy = policy
+        self.age_s = float(age_s)
         self.opts = opts
         self.streams = [torch.cuda.Stream() for _ in range(int(n_streams))]
         self.free_slots = list(range(len(self.streams)))
@@ -106,12 +114,20 @@ class Server:
         # scores (device + flags) + profile + a fixed allowance for the plan and boundary strips
         return len(reqs) * n * 8 + 21 * 4 * (m + 1024 * len(reqs)) + (256 << 20)
 
+    def _order(self, now):
+        """Pending requests in admission order."""
+        if self.policy == "fifo":
+            return list(self.pending)
+        aged = [r for r in self.pending if now - r.arrival >= self.age_s]
+        young = sorted((r for r in self.pending if now - r.arrival < self.age_s), key=lambda r: len(r.query))
+        return aged + young
+
     def _admit(self):
         with self.lock:
             if not self.pending or not self.free_slots:
                 return False
             take = []
-            for r in self.pending:
+            for r in self._order(time.perf_counter()):
                 if len(take) >= self.max_batch:
                     break
                 if self.mem_used + self._batch_bytes(take + [r]) > self.mem_budget and take:
@@ -120,7 +136,8 @@ class Server:
             need = self._batch_bytes(take)
             if self.mem_used + need > self.mem_budget and self.inflight:
                 return False  # wait for memory to free up
-            self.pending = self.pending[len(take):]
+            chosen = set(map(id, take))
+            self.pending = [r for r in self.pending if id(r) not in chosen]
             slot = self.free_slots.pop(0)
             self.mem_used += need
         torch = self.torch
