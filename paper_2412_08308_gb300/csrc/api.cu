@@ -361,19 +361,23 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   if (n_long < Q->n_units) max_short = unit_len(n_long);
   if (n_long) max_long = unit_len(0);
   // fill[L]: steps a chain of L lanes spends per real column of a short unit.
-  // A pass over a unit of n padded columns takes n + L - 1 steps rounded up to
-  // whole 16-column blocks.
-  double fill[33];
-  {
-    std::vector<int64_t> hist(max_short / kColBlock + 1, 0);
-    for (int64_t u = n_long; u < Q->n_units; ++u) ++hist[unit_len(u) / kColBlock];
+  // A pass over a unit of n padded columns takes n + lag steps (lag = L - 1,
+  // or 2 L - 1 for the split lanes of the 16-bit forms) rounded up to whole
+  // 16-column blocks.  fill for the solo plans of this mode; fillq (below)
+  // for the query-pair plans.
+  std::vector<int64_t> len_hist(max_short / kColBlock + 1, 0);
+  for (int64_t u = n_long; u < Q->n_units; ++u) ++len_hist[unit_len(u) / kColBlock];
+  auto make_fill = [&](int form, double *out) {
     for (int L = 0; L <= 32; ++L) {
+      const int lag = L > 0 ? inter_chain_lag(R, form, L) : 0;
       double steps = 0;
-      for (size_t b = 1; b < hist.size(); ++b)
-        steps += (double)hist[b] * (double)((b * kColBlock + L - 1 + kColBlock - 1) / kColBlock * kColBlock);
-      fill[L] = sum_short > 0 ? steps / sum_short : 1.0;
+      for (size_t b = 1; b < len_hist.size(); ++b)
+        steps += (double)len_hist[b] * (double)((b * kColBlock + lag + kColBlock - 1) / kColBlock * kColBlock);
+      out[L] = sum_short > 0 ? steps / sum_short : 1.0;
     }
-  }
+  };
+  double fill[33];
+  make_fill(packed ? kFormPacked : kFormInt32, fill);
 
   // --- rows per lane and CTA size of the inter-task kernel.  A small batch
   // (few units x queries) cannot fill the GPU with 16-row lanes: halve the
@@ -450,6 +454,8 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   // favour pairs: each pair's L fits its length; few queries of spread-out
   // lengths favour tracks: no idle half.)
   auto chunks_of = [&](int32_t q, int L) { return std::max(1, (qlen(q) + L * R - 1) / (L * R)); };
+  double fillq[33];
+  make_fill(kFormQPair, fillq);
   // best L for a group packed into two tracks, and its modelled cost
   auto plan_group = [&](const std::vector<int32_t> &grp, std::vector<int32_t> *tr, int *Lout) {
     auto pack = [&](int L, std::vector<int32_t> *out) {
@@ -463,7 +469,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
     };
     auto cost_of = [&](int L) {
       const double eff = (double)((32 / L) * L) / 32.0;
-      return (double)pack(L, nullptr) * L * R * fill[L] / eff * (1.0 + 0.001 * (double)pack(L, nullptr) /
+      return (double)pack(L, nullptr) * L * R * fillq[L] / eff * (1.0 + 0.001 * (double)pack(L, nullptr) /
                                                                           std::max<size_t>(1, grp.size()) * 2);
     };
     int Lp = 4;

@@ -214,6 +214,74 @@ __device__ __forceinline__ void column_step(LaneState<R, FORM> &st, const uint8_
   st.hdiag = inH;
 }
 
+// 16-bit forms with two independent half-chains per lane: rows [0, R/2) at
+// column c and rows [R/2, R) at column c - 1, one step behind, so that the
+// two F/H dependency chains down the rows interleave.  The upper half's F
+// output and its bottom H feed the lower half one step later (midF, hdiagB);
+// the lane passes on the lower half's bottom row, of column c - 1, so lane
+// k + 1 works two columns behind lane k.  resA / resB: the residue code(s) of
+// column c / c - 1.  S and S2 keep the halves' running best.
+template <int R, int FORM>
+__device__ __forceinline__ void column_step_split(LaneState<R, FORM> &st, uint32_t &hdiagB, uint32_t &midF,
+                                                  const uint8_t *prow, int stride, uint32_t resA, uint32_t resB,
+                                                  uint32_t inH, uint32_t inF, const Consts &cs, uint32_t &S,
+                                                  uint32_t &S2, uint32_t &outH, uint32_t &outF, int gstride) {
+  static_assert(FORM != kFormInt32 && R % 8 == 0, "16-bit forms, halves of whole 4-row groups");
+  constexpr int H2 = R / 2;
+  // substitution words of the upper half (column c) and the lower half (column c - 1)
+  uint32_t pa[H2], pb[H2];
+  if constexpr (FORM == kFormQPair) {
+#pragma unroll
+    for (int i = 0; i < H2 / 4; ++i) {
+      const uint4 v = *reinterpret_cast<const uint4 *>(prow + (resA & 0xffu) * stride + i * gstride);
+      pa[4 * i + 0] = v.x; pa[4 * i + 1] = v.y; pa[4 * i + 2] = v.z; pa[4 * i + 3] = v.w;
+      const uint4 w = *reinterpret_cast<const uint4 *>(prow + (resB & 0xffu) * stride + (H2 / 4 + i) * gstride);
+      pb[4 * i + 0] = w.x; pb[4 * i + 1] = w.y; pb[4 * i + 2] = w.z; pb[4 * i + 3] = w.w;
+    }
+  } else {
+    // two database sequences: each word pairs their profile bytes (PRMT)
+    uint32_t a0[H2 / 4], a1[H2 / 4], b0[H2 / 4], b1[H2 / 4];
+    load_prof<H2>(prow + (resA & 0xffu) * stride, a0);
+    load_prof<H2>(prow + (resA >> 16) * stride, a1);
+    load_prof<H2>(prow + (resB & 0xffu) * stride + H2, b0);
+    load_prof<H2>(prow + (resB >> 16) * stride + H2, b1);
+#pragma unroll
+    for (int r = 0; r < H2; ++r) {
+      pa[r] = prmt(a0[r >> 2], a1[r >> 2], sel_pair(r & 3));
+      pb[r] = prmt(b0[r >> 2], b1[r >> 2], sel_pair(r & 3));
+    }
+  }
+  const uint32_t diagB_next = (uint32_t)st.Hl[H2 - 1];  // H of the upper half's last row at column c - 1
+  // lower half first in program order (its inputs are ready), then the upper
+  uint32_t hd = hdiagB, f = midF, s2 = S2;
+#pragma unroll
+  for (int r = H2; r < R; ++r) {
+    uint32_t e = (uint32_t)st.E[r];
+    const uint32_t h = cell_word(hd, pb[r - H2], e, f, s2, cs);
+    st.E[r] = e;
+    hd = (uint32_t)st.Hl[r];
+    st.Hl[r] = h;
+  }
+  outH = (uint32_t)st.Hl[R - 1];
+  outF = f;
+  S2 = s2;
+  hd = (uint32_t)st.hdiag;
+  f = inF;
+  uint32_t s = S;
+#pragma unroll
+  for (int r = 0; r < H2; ++r) {
+    uint32_t e = (uint32_t)st.E[r];
+    const uint32_t h = cell_word(hd, pa[r], e, f, s, cs);
+    st.E[r] = e;
+    hd = (uint32_t)st.Hl[r];
+    st.Hl[r] = h;
+  }
+  S = s;
+  midF = f;
+  hdiagB = diagB_next;
+  st.hdiag = inH;
+}
+
 template <int FORM>
 __device__ __forceinline__ Word<FORM> score_max(Word<FORM> a, Word<FORM> b) {
   if constexpr (FORM != kFormInt32) return (Word<FORM>)__vmaxs2((uint32_t)a, (uint32_t)b);

@@ -161,6 +161,9 @@ cudaError_t launch_trace(const TraceArgs &a, cudaStream_t s);
 // launchers (k_inter.cu)
 int inter_threads();
 bool inter_supported_R(int R);
+// Steps between a chain's first lane reaching a column and its last lane
+// leaving it (L - 1; 2 L - 1 for the split query-pair lanes).
+int inter_chain_lag(int R, int form, int L);
 size_t inter_smem_bytes(int pbuf_bytes, int pbuf_count, int threads);
 cudaError_t launch_inter(const InterArgs &a, int R, int form, int grid, int threads, size_t smem,
                          cudaStream_t s);

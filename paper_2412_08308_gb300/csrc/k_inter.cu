@@ -45,6 +45,14 @@ constexpr int kThreads = 256;
 constexpr int kChainsPerWarpMax = 8;  // lanes per chain >= 4
 constexpr int kRingBytes = 320;       // residues: 2 slots x 2 seqs x 16 B; boundary: 2 slots x 16 x 8 B
 
+// 16-bit forms with split lanes (column_step_split): two half-chains per
+// lane, lanes two columns apart.
+template <int R, int FORM>
+constexpr bool kSplit = FORM != kFormInt32 && R % 8 == 0;
+// steps from a chain's first lane reaching a column to its last lane leaving it
+template <int R, int FORM>
+__host__ __device__ constexpr int chain_lag(int L) { return kSplit<R, FORM> ? 2 * L - 1 : L - 1; }
+
 // One pass of a chain over all columns of its unit for the rows of one chunk.
 // restart (16-bit forms): halves whose rows start a new query in this chunk;
 // they take the matrix top boundary instead of the strip of the chunk above.
@@ -59,12 +67,15 @@ __device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, cons
   using W = Word<FORM>;
   constexpr bool PACKED = FORM != kFormInt32;      // 16-bit halves
   constexpr bool PAIRS = FORM == kFormPacked;      // two database sequences per unit
+  constexpr bool SPLIT = kSplit<R, FORM>;
   const W H0 = (W)0;
   const W F0 = PACKED ? (W)cs.F0W : (W)0;
   LaneState<R, FORM> st;
   lane_reset(st, cs);
   W outH = H0, outF = F0;
   uint32_t outRes = kPadPair;
+  // split lanes: the lower half's residue, diagonal H and incoming F, best
+  uint32_t prevRes = kPadPair, hdiagB = 0u, midF = (uint32_t)F0, S2 = 0u;
   const int src = (k > 0) ? lane - 1 : lane;
   const bool lead = live && k == 0;
   const bool tail = live && (k == L - 1) && next;
@@ -136,10 +147,21 @@ __device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, cons
             inF = F0;
           }
         }
-        column_step<R, FORM>(st, prow, stride, inRes, inH, inF, cs, S, outH, outF, gstride);
-        outRes = inRes;
+        if constexpr (SPLIT) {
+          uint32_t s = (uint32_t)S, oh, of;
+          column_step_split<R, FORM>(st, hdiagB, midF, prow, stride, inRes, prevRes, (uint32_t)inH, (uint32_t)inF,
+                                     cs, s, S2, oh, of, gstride);
+          S = (W)s;
+          outH = (W)oh;
+          outF = (W)of;
+          outRes = prevRes;
+          prevRes = inRes;
+        } else {
+          column_step<R, FORM>(st, prow, stride, inRes, inH, inF, cs, S, outH, outF, gstride);
+          outRes = inRes;
+        }
         if (tail) {
-          const int j = t - (L - 1);
+          const int j = t - chain_lag<R, FORM>(L);
           if (j >= 0 && j < npad) gb[j] = make_uint2((uint32_t)outH, (uint32_t)outF);
         }
       }
@@ -150,6 +172,7 @@ __device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, cons
     }
   }
   if (lead) cp_async_wait<0>();
+  if constexpr (SPLIT) S = score_max<FORM>(S, (W)S2);
 }
 
 template <int R, int FORM>
@@ -202,7 +225,8 @@ __global__ void __launch_bounds__(kThreads, 2) inter_kernel(const InterArgs a) {
       npb = PAIRS ? a.db.npad[posB] : 0;
     }
     const int npad = max(npa, npb);
-    const int nblk = __reduce_max_sync(0xffffffffu, live ? (npad + L - 1 + kColBlock - 1) / kColBlock : 0);
+    const int nblk =
+        __reduce_max_sync(0xffffffffu, live ? (npad + chain_lag<R, FORM>(L) + kColBlock - 1) / kColBlock : 0);
     const uint8_t *resA = a.db.res + (live ? a.db.off[posA] : 0);
     const uint8_t *resB = a.db.res + (live ? a.db.off[posB] : 0);
     const int cslot = warp * kChainsPerWarpMax + min(cw, kChainsPerWarpMax - 1);
@@ -310,6 +334,18 @@ bool inter_supported_R(int R) {
   SWGB_INTER_R_LIST(SWGB_CASE)
 #undef SWGB_CASE
   return false;
+}
+
+int inter_chain_lag(int R, int form, int L) {
+#define SWGB_CASE(RR)                                                    \
+  if (R == RR) {                                                         \
+    if (form == kFormInt32) return chain_lag<RR, kFormInt32>(L);        \
+    if (form == kFormPacked) return chain_lag<RR, kFormPacked>(L);      \
+    if (form == kFormQPair) return chain_lag<RR, kFormQPair>(L);        \
+  }
+  SWGB_INTER_R_LIST(SWGB_CASE)
+#undef SWGB_CASE
+  return L - 1;
 }
 
 cudaError_t launch_inter(const InterArgs &a, int R, int form, int grid, int threads, size_t smem,
