@@ -83,27 +83,59 @@ __device__ __forceinline__ void load_prof(const uint8_t *p, uint32_t (&w)[R / 4]
   }
 }
 
+// N profile bytes at byte OFF of an 8-byte-aligned slot, as N/4 words, by the
+// widest aligned loads (the halves of a 24-byte slot start at 0 and 12).
+template <int N, int OFF, int W = 0>
+__device__ __forceinline__ void load_prof_at(const uint8_t *p, uint32_t (&w)[N / 4]) {
+  static_assert(N % 4 == 0 && OFF % 4 == 0, "whole words");
+  constexpr int b = 4 * W;
+  if constexpr (b < N) {
+    if constexpr ((OFF + b) % 8 == 0 && b + 8 <= N) {
+      const uint2 v = *reinterpret_cast<const uint2 *>(p + OFF + b);
+      w[W] = v.x;
+      w[W + 1] = v.y;
+      load_prof_at<N, OFF, W + 2>(p, w);
+    } else {
+      w[W] = *reinterpret_cast<const uint32_t *>(p + OFF + b);
+      load_prof_at<N, OFF, W + 1>(p, w);
+    }
+  }
+}
+
 __device__ __forceinline__ uint32_t word_of(const uint4 &v, int i) {
   return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
 }
 
-// One 32-bit word of two 16-bit cells (Eqs. 1-3 per half).  hd is H of the
-// diagonal neighbour, p the substitution scores; E (this row) and f (passed
-// down the column) are updated in place, S keeps the running best.  Five
-// maxima (the zero floor rides on the first) and four per-half additions;
-// H - Go is shared by the E and F updates.  (Computing the next F from
-// max(hd + p, E, 0) - Go instead of H - Go, which is equal because
-// Ge <= Go, shortens the chain down the column but costs a fifth addition
-// and measured slower.)
-__device__ __forceinline__ uint32_t cell_word(uint32_t hd, uint32_t p, uint32_t &E, uint32_t &f, uint32_t &S,
-                                              const Consts &cs) {
-  const uint32_t tt = __vimax_s16x2_relu(__vadd2(hd, p), E);  // max(hd + SM, E, 0)
-  const uint32_t h = __vmaxs2(tt, f);
-  S = __vmaxs2(S, h);
-  const uint32_t hgo = __vsub2(h, cs.goW);
-  E = __vmaxs2(__vsub2(E, cs.geW), hgo);
-  f = __vmaxs2(__vsub2(f, cs.geW), hgo);
-  return h;
+// N rows [R0, R0 + N) of one column, 32-bit words of two 16-bit cells
+// (Eqs. 1-3 per half).  hd0 is H of the row above R0 at the previous column,
+// p the rows' substitution words; E (per row, this column) and f (passed down
+// the column) are updated in place, S keeps the running best.  Per word five
+// maxima, the zero floor riding on the one with F, and four per-half
+// additions, H - Go shared by the E and F updates.  The terms that do not
+// depend on the row above, max(H_diag + SM, E), are formed for all N rows
+// first: the previous column's H is then dead before any row is rewritten
+// (no register copies), and only max(., F), the subtraction and the F update
+// remain on the chain down the rows.  (Computing the next F from
+// max(hd + p, E, 0) - Go instead of H - Go, which is equal because Ge <= Go,
+// shortens that chain further but costs a fifth addition and measured
+// slower.)
+template <int R0, int N, int R>
+__device__ __forceinline__ void word_rows(uint32_t hd0, const uint32_t (&p)[N], uint32_t (&E)[R],
+                                          uint32_t (&Hl)[R], uint32_t &f, uint32_t &S, const Consts &cs) {
+  static_assert(R0 + N <= R, "rows in range");
+  uint32_t tt[N];
+  tt[0] = __vmaxs2(__vadd2(hd0, p[0]), E[R0]);
+#pragma unroll
+  for (int r = 1; r < N; ++r) tt[r] = __vmaxs2(__vadd2(Hl[R0 + r - 1], p[r]), E[R0 + r]);
+#pragma unroll
+  for (int r = 0; r < N; ++r) {
+    const uint32_t h = __vimax_s16x2_relu(tt[r], f);  // max(H_diag + SM, E, F, 0)
+    S = __vmaxs2(S, h);
+    const uint32_t hgo = __vsub2(h, cs.goW);
+    E[R0 + r] = __vmaxs2(__vsub2(E[R0 + r], cs.geW), hgo);
+    f = __vmaxs2(__vsub2(f, cs.geW), hgo);
+    Hl[R0 + r] = h;
+  }
 }
 
 template <int FORM>
@@ -151,15 +183,8 @@ __device__ __forceinline__ void column_step(LaneState<R, FORM> &st, const uint8_
       const uint4 v = *reinterpret_cast<const uint4 *>(prow + (res & 0xffu) * stride + i * gstride);
       pw[4 * i + 0] = v.x; pw[4 * i + 1] = v.y; pw[4 * i + 2] = v.z; pw[4 * i + 3] = v.w;
     }
-    uint32_t hd = (uint32_t)st.hdiag, f = (uint32_t)inF, s = (uint32_t)S;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      uint32_t e = (uint32_t)st.E[r];
-      const uint32_t h = cell_word(hd, pw[r], e, f, s, cs);
-      st.E[r] = (W)e;
-      hd = (uint32_t)st.Hl[r];
-      st.Hl[r] = (W)h;
-    }
+    uint32_t f = (uint32_t)inF, s = (uint32_t)S;
+    word_rows<0, R>((uint32_t)st.hdiag, pw, st.E, st.Hl, f, s, cs);
     S = (W)s;
     outH = st.Hl[R - 1];
     outF = (W)f;
@@ -172,16 +197,11 @@ __device__ __forceinline__ void column_step(LaneState<R, FORM> &st, const uint8_
   if constexpr (PACKED) {
     uint32_t pb[R / 4];
     load_prof<R>(prow + (res >> 16) * stride, pb);
-    uint32_t hd = (uint32_t)st.hdiag, f = (uint32_t)inF, s = (uint32_t)S;
+    uint32_t pw[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const uint32_t p = prmt(pa[r >> 2], pb[r >> 2], sel_pair(r & 3));  // (SM_a, SM_b), signed halves
-      uint32_t e = (uint32_t)st.E[r];
-      const uint32_t h = cell_word(hd, p, e, f, s, cs);
-      st.E[r] = (W)e;
-      hd = (uint32_t)st.Hl[r];
-      st.Hl[r] = (W)h;
-    }
+    for (int r = 0; r < R; ++r) pw[r] = prmt(pa[r >> 2], pb[r >> 2], sel_pair(r & 3));  // (SM_a, SM_b), signed halves
+    uint32_t f = (uint32_t)inF, s = (uint32_t)S;
+    word_rows<0, R>((uint32_t)st.hdiag, pw, st.E, st.Hl, f, s, cs);
     S = (W)s;
     outH = st.Hl[R - 1];
     outF = (W)f;
@@ -241,41 +261,26 @@ __device__ __forceinline__ void column_step_split(LaneState<R, FORM> &st, uint32
   } else {
     // two database sequences: each word pairs their profile bytes (PRMT)
     uint32_t a0[H2 / 4], a1[H2 / 4], b0[H2 / 4], b1[H2 / 4];
-    load_prof<H2>(prow + (resA & 0xffu) * stride, a0);
-    load_prof<H2>(prow + (resA >> 16) * stride, a1);
-    load_prof<H2>(prow + (resB & 0xffu) * stride + H2, b0);
-    load_prof<H2>(prow + (resB >> 16) * stride + H2, b1);
+    load_prof_at<H2, 0>(prow + (resA & 0xffu) * stride, a0);
+    load_prof_at<H2, 0>(prow + (resA >> 16) * stride, a1);
+    load_prof_at<H2, H2>(prow + (resB & 0xffu) * stride, b0);
+    load_prof_at<H2, H2>(prow + (resB >> 16) * stride, b1);
 #pragma unroll
     for (int r = 0; r < H2; ++r) {
       pa[r] = prmt(a0[r >> 2], a1[r >> 2], sel_pair(r & 3));
       pb[r] = prmt(b0[r >> 2], b1[r >> 2], sel_pair(r & 3));
     }
   }
-  const uint32_t diagB_next = (uint32_t)st.Hl[H2 - 1];  // H of the upper half's last row at column c - 1
+  const uint32_t diagB_next = st.Hl[H2 - 1];  // H of the upper half's last row at column c - 1
   // lower half first in program order (its inputs are ready), then the upper
-  uint32_t hd = hdiagB, f = midF, s2 = S2;
-#pragma unroll
-  for (int r = H2; r < R; ++r) {
-    uint32_t e = (uint32_t)st.E[r];
-    const uint32_t h = cell_word(hd, pb[r - H2], e, f, s2, cs);
-    st.E[r] = e;
-    hd = (uint32_t)st.Hl[r];
-    st.Hl[r] = h;
-  }
-  outH = (uint32_t)st.Hl[R - 1];
+  uint32_t f = midF, s2 = S2;
+  word_rows<H2, H2>(hdiagB, pb, st.E, st.Hl, f, s2, cs);
+  outH = st.Hl[R - 1];
   outF = f;
   S2 = s2;
-  hd = (uint32_t)st.hdiag;
   f = inF;
   uint32_t s = S;
-#pragma unroll
-  for (int r = 0; r < H2; ++r) {
-    uint32_t e = (uint32_t)st.E[r];
-    const uint32_t h = cell_word(hd, pa[r], e, f, s, cs);
-    st.E[r] = e;
-    hd = (uint32_t)st.Hl[r];
-    st.Hl[r] = h;
-  }
+  word_rows<0, H2>(st.hdiag, pa, st.E, st.Hl, f, s, cs);
   S = s;
   midF = f;
   hdiagB = diagB_next;

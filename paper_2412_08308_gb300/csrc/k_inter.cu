@@ -97,6 +97,11 @@ __device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, cons
     if (prev && col < npad) {
 #pragma unroll
       for (int i = 0; i < 8; ++i) cp_async16(rgb + slot * 16 + 2 * i, gb + col + 2 * i);
+    } else {
+      // the matrix top boundary (first chunk, or padding columns)
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        reinterpret_cast<uint4 *>(rgb + slot * 16)[i] = make_uint4((uint32_t)H0, (uint32_t)F0, (uint32_t)H0, (uint32_t)F0);
     }
     cp_async_commit();
   };
@@ -108,9 +113,9 @@ __device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, cons
   for (int blk = 0; blk < nblk; ++blk) {
     uint4 ra4 = make_uint4(0, 0, 0, 0), rb4 = make_uint4(0, 0, 0, 0);
     uint2 *gslot = rgb + (blk & 1) * 16;
-    // lane 0's columns of this block are all real or all padding (npad is a multiple of 16)
-    const bool real = blk * kColBlock < npad;
-    const bool from_strip = prev && real;
+    // lane 0's columns of this block are all real or all padding (npad is a
+    // multiple of 16); real ones of a later chunk come from the strip
+    const bool from_strip = prev && blk * kColBlock < npad;
     if (lead) {
       cp_async_wait<1>();
       ra4 = *reinterpret_cast<const uint4 *>(rres + (blk & 1) * 32);
@@ -136,16 +141,12 @@ __device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, cons
         W inF = (W)__shfl_sync(0xffffffffu, outF, src);
         uint32_t inRes = __shfl_sync(0xffffffffu, outRes, src);
         if (k == 0) {
-          const uint32_t rr = PAIRS ? prmt(wa, wb, sel_pair(s4)) : prmt(wa, 0u, sel_one(s4));
-          inRes = real ? rr : kPadPair;
-          if (from_strip) {
-            const uint2 v = gslot[s];
-            inH = (W)v.x;
-            inF = (W)v.y;
-          } else {
-            inH = H0;
-            inF = F0;
-          }
+          // (the residue ring holds the pad code past the end of a sequence,
+          // the boundary slot the top boundary where there is no chunk above)
+          inRes = PAIRS ? prmt(wa, wb, sel_pair(s4)) : prmt(wa, 0u, sel_one(s4));
+          const uint2 v = gslot[s];
+          inH = (W)v.x;
+          inF = (W)v.y;
         }
         if constexpr (SPLIT) {
           uint32_t s = (uint32_t)S, oh, of;
@@ -162,7 +163,7 @@ __device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, cons
         }
         if (tail) {
           const int j = t - chain_lag<R, FORM>(L);
-          if (j >= 0 && j < npad) gb[j] = make_uint2((uint32_t)outH, (uint32_t)outF);
+          if ((unsigned)j < (unsigned)npad) gb[j] = make_uint2((uint32_t)outH, (uint32_t)outF);
         }
       }
     }
