@@ -165,8 +165,9 @@ __device__ __forceinline__ void lane_reset(LaneState<R, FORM> &st, const Consts 
 // One column: inputs are the (H, F) pair passed down from the row above this
 // lane's rows and the residue code(s) of the column; prow points at this
 // lane's R profile entries of residue row 0 (rows are `stride` bytes apart).
-// Query-pair form: prow points at this lane's first 16-byte group of four
-// words; its R/4 groups are `gstride` bytes apart (lanes interleaved, so the
+// Query-pair form: res is the bare residue code (no second code in the high
+// half); prow points at this lane's first 16-byte group of four words; its
+// R/4 groups are `gstride` bytes apart (lanes interleaved, so the
 // 32 lanes of a warp read 32 consecutive 16-byte groups: no bank conflict).
 // Outputs the (H, F) pair for the row below: int32 passes (H, F) of the last
 // row; packed passes (H of the last row, F of the row below it).
@@ -180,7 +181,7 @@ __device__ __forceinline__ void column_step(LaneState<R, FORM> &st, const uint8_
     uint32_t pw[R];
 #pragma unroll
     for (int i = 0; i < R / 4; ++i) {
-      const uint4 v = *reinterpret_cast<const uint4 *>(prow + (res & 0xffu) * stride + i * gstride);
+      const uint4 v = *reinterpret_cast<const uint4 *>(prow + res * stride + i * gstride);
       pw[4 * i + 0] = v.x; pw[4 * i + 1] = v.y; pw[4 * i + 2] = v.z; pw[4 * i + 3] = v.w;
     }
     uint32_t f = (uint32_t)inF, s = (uint32_t)S;
@@ -253,9 +254,9 @@ __device__ __forceinline__ void column_step_split(LaneState<R, FORM> &st, uint32
   if constexpr (FORM == kFormQPair) {
 #pragma unroll
     for (int i = 0; i < H2 / 4; ++i) {
-      const uint4 v = *reinterpret_cast<const uint4 *>(prow + (resA & 0xffu) * stride + i * gstride);
+      const uint4 v = *reinterpret_cast<const uint4 *>(prow + resA * stride + i * gstride);
       pa[4 * i + 0] = v.x; pa[4 * i + 1] = v.y; pa[4 * i + 2] = v.z; pa[4 * i + 3] = v.w;
-      const uint4 w = *reinterpret_cast<const uint4 *>(prow + (resB & 0xffu) * stride + (H2 / 4 + i) * gstride);
+      const uint4 w = *reinterpret_cast<const uint4 *>(prow + resB * stride + (H2 / 4 + i) * gstride);
       pb[4 * i + 0] = w.x; pb[4 * i + 1] = w.y; pb[4 * i + 2] = w.z; pb[4 * i + 3] = w.w;
     }
   } else {

@@ -73,9 +73,11 @@ __device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, cons
   LaneState<R, FORM> st;
   lane_reset(st, cs);
   W outH = H0, outF = F0;
-  uint32_t outRes = kPadPair;
+  // residue code(s) of the column; one database sequence: the bare code
+  constexpr uint32_t kPadRes = PAIRS ? kPadPair : (uint32_t)kPadCode;
+  uint32_t outRes = kPadRes;
   // split lanes: the lower half's residue, diagonal H and incoming F, best
-  uint32_t prevRes = kPadPair, hdiagB = 0u, midF = (uint32_t)F0, S2 = 0u;
+  uint32_t prevRes = kPadRes, hdiagB = 0u, midF = (uint32_t)F0, S2 = 0u;
   const int src = (k > 0) ? lane - 1 : lane;
   const bool lead = live && k == 0;
   const bool tail = live && (k == L - 1) && next;
