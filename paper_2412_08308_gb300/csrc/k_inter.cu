@@ -113,15 +113,13 @@ __device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, cons
   }
 
   for (int blk = 0; blk < nblk; ++blk) {
-    uint4 ra4 = make_uint4(0, 0, 0, 0), rb4 = make_uint4(0, 0, 0, 0);
+    const uint32_t *rw = reinterpret_cast<const uint32_t *>(rres + (blk & 1) * 32);  // this block's residue words
     uint2 *gslot = rgb + (blk & 1) * 16;
     // lane 0's columns of this block are all real or all padding (npad is a
     // multiple of 16); real ones of a later chunk come from the strip
     const bool from_strip = prev && blk * kColBlock < npad;
     if (lead) {
       cp_async_wait<1>();
-      ra4 = *reinterpret_cast<const uint4 *>(rres + (blk & 1) * 32);
-      if (PAIRS) rb4 = *reinterpret_cast<const uint4 *>(rres + (blk & 1) * 32 + 16);
       if (PACKED && restart && from_strip) {  // (this thread's own cp.async data, already landed)
 #pragma unroll
         for (int i = 0; i < kColBlock; ++i) {
@@ -134,7 +132,8 @@ __device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, cons
     // body small enough for the instruction cache
 #pragma unroll 1
     for (int g4 = 0; g4 < kColBlock / 4; ++g4) {
-      const uint32_t wa = word_of(ra4, g4), wb = word_of(rb4, g4);
+      // four residues of each sequence (used by the lead lane only)
+      const uint32_t wa = rw[g4], wb = PAIRS ? rw[4 + g4] : 0u;
 #pragma unroll
       for (int s4 = 0; s4 < 4; ++s4) {
         const int s = g4 * 4 + s4;
@@ -142,9 +141,11 @@ __device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, cons
         W inH = (W)__shfl_sync(0xffffffffu, outH, src);
         W inF = (W)__shfl_sync(0xffffffffu, outF, src);
         uint32_t inRes = __shfl_sync(0xffffffffu, outRes, src);
-        if (k == 0) {
+        if (lead) {
           // (the residue ring holds the pad code past the end of a sequence,
-          // the boundary slot the top boundary where there is no chunk above)
+          // the boundary slot the top boundary where there is no chunk above;
+          // the first lane of a chain without a unit keeps its own pad values,
+          // its ring is never filled)
           inRes = PAIRS ? prmt(wa, wb, sel_pair(s4)) : prmt(wa, 0u, sel_one(s4));
           const uint2 v = gslot[s];
           inH = (W)v.x;
