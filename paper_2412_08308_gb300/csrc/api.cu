@@ -110,6 +110,9 @@ struct sw_queries {
   cudaStream_t alloc_stream = nullptr;
   cudaStream_t side = nullptr;  // second stream for the intra-task kernel
   cudaEvent_t fork = nullptr, join = nullptr;
+  // third stream: the int32 intra-task launch beside the packed one
+  cudaStream_t side2 = nullptr;
+  cudaEvent_t join2 = nullptr;
   uint8_t *d_qres = nullptr;
   int8_t *d_submat = nullptr;
   QDesc *d_qd = nullptr, *d_qdi = nullptr, *d_qdp = nullptr;
@@ -172,6 +175,8 @@ void free_queries(sw_queries *q) {
   if (q->fork) cudaEventDestroy(q->fork);
   if (q->join) cudaEventDestroy(q->join);
   if (q->side) cudaStreamDestroy(q->side);
+  if (q->join2) cudaEventDestroy(q->join2);
+  if (q->side2) cudaStreamDestroy(q->side2);
   delete q;
 }
 
@@ -768,7 +773,9 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   const size_t b_units = round_up(4 * (int64_t)units.size(), 256);
   const size_t b_prof = round_up(Q->prof_bytes, 256);
   const size_t b_gbuf = round_up((int64_t)gslots * warps * 8 * (int64_t)Q->gbuf_stride * 8, 256);
-  const size_t b_igbuf = round_up((int64_t)Q->igrid * (int64_t)Q->igbuf_stride * 8, 256);
+  // (two intra-task launches at once, packed and int32, each with its strips)
+  const int ilaunches = Q->n_itasks && Q->n_itasks32 ? 2 : 1;
+  const size_t b_igbuf = round_up((int64_t)ilaunches * Q->igrid * (int64_t)Q->igbuf_stride * 8, 256);
   const size_t b_words = round_up(4 * (12 + 2 * nqm), 256);  // zeroed words + 3 constants
   const size_t b_flag = Q->inter_may_flag ? round_up(4 * nqm * std::max<int64_t>(n, 1), 256) : 0;
   const size_t b_iflag = packed ? round_up(4 * nqm * Q->long_stride, 256) : 0;
@@ -854,6 +861,10 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
     e = cudaStreamCreateWithFlags(&Q->side, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&Q->fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&Q->join, cudaEventDisableTiming);
+    if (e == cudaSuccess && Q->n_itasks && Q->n_itasks32) {
+      e = cudaStreamCreateWithFlags(&Q->side2, cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&Q->join2, cudaEventDisableTiming);
+    }
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
@@ -902,10 +913,13 @@ int sw_search_prepared(const sw_db *db, const sw_queries *Q, int32_t *scores_dev
   a.sc = Q->sc;
   a.status = w + 2;
 
-  // long database units: intra-task kernel on the side stream, concurrently
+  // long database units: intra-task kernel on the side stream, concurrently;
+  // int32 matrices (those that could saturate 16 bits) on a third stream
+  // when packed ones exist too, so that neither waits for the other
   if (Q->n_long) {
     SW_CUDA(cudaEventRecord(Q->fork, s), "event");
     SW_CUDA(cudaStreamWaitEvent(Q->side, Q->fork, 0), "event");
+    if (Q->side2) SW_CUDA(cudaStreamWaitEvent(Q->side2, Q->fork, 0), "event");
     InterArgs b = a;
     b.qd = Q->d_qdi;
     b.pbuf_bytes = Q->ipbuf_bytes;
@@ -925,7 +939,13 @@ int sw_search_prepared(const sw_db *db, const sw_queries *Q, int32_t *scores_dev
       b.tasks = Q->d_itasks32;
       b.n_tasks = w + Q->zero_words() + 2;
       b.task_counter = w + 5;
-      SW_CUDA(launch_intra(b, Q->Ri, false, Q->igrid, Q->ismem, Q->side), "intra-task kernel (int32)");
+      cudaStream_t st = Q->side;
+      if (Q->side2) {
+        st = Q->side2;
+        b.gbuf = Q->d_igbuf + (size_t)Q->igrid * Q->igbuf_stride;
+      }
+      SW_CUDA(launch_intra(b, Q->Ri, false, Q->igrid, Q->ismem, st), "intra-task kernel (int32)");
+      if (Q->side2) SW_CUDA(cudaEventRecord(Q->join2, Q->side2), "event");
     }
     SW_CUDA(cudaEventRecord(Q->join, Q->side), "event");
   }
@@ -981,6 +1001,7 @@ int sw_search_prepared(const sw_db *db, const sw_queries *Q, int32_t *scores_dev
     }
   }
   if (Q->n_long) SW_CUDA(cudaStreamWaitEvent(s, Q->join, 0), "event");
+  if (Q->side2) SW_CUDA(cudaStreamWaitEvent(s, Q->join2, 0), "event");
   return SW_OK;
 }
 
