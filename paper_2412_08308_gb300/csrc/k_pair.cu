@@ -137,6 +137,14 @@ __device__ __forceinline__ bool band_pass(const uint8_t *__restrict__ pch, const
       if (lead) st_release(x.cons_in, consumed);
     }
   };
+  // both boundary slots start as the matrix top boundary (the band without
+  // a band above keeps it; the others overwrite block by block, and the two
+  // padding blocks at the end get it back below)
+  if (lane < kColBlock) {
+    rgb[lane] = make_uint2(0u, 0u);
+    rgb[kColBlock + lane] = make_uint2(0u, 0u);
+  }
+  __syncwarp();
   if (prev) {
     load();
     land(0);
@@ -165,17 +173,12 @@ __device__ __forceinline__ bool band_pass(const uint8_t *__restrict__ pch, const
       failed = true;
       break;
     }
-    uint4 ra4 = make_uint4(0, 0, 0, 0);
     const uint2 *gslot = rgb + (blk & 1) * kColBlock;
-    const bool real = blk < nreal;
-    const bool from_strip = prev && real;
-    if (lead) {
-      cp_async_wait<1>();
-      ra4 = *reinterpret_cast<const uint4 *>(rres + (blk & 1) * 32);
-    }
+    const uint32_t *rw = reinterpret_cast<const uint32_t *>(rres + (blk & 1) * 32);  // this block's residues
+    if (lead) cp_async_wait<1>();
 #pragma unroll 1
     for (int g4 = 0; g4 < kColBlock / 4; ++g4) {
-      const uint32_t wa = word_of(ra4, g4);
+      const uint32_t wa = rw[g4];  // (used by lane 0 only)
 #pragma unroll
       for (int s4 = 0; s4 < 4; ++s4) {
         const int s = g4 * 4 + s4;
@@ -184,15 +187,12 @@ __device__ __forceinline__ bool band_pass(const uint8_t *__restrict__ pch, const
         W inF = (W)__shfl_sync(0xffffffffu, outF, src);
         uint32_t inRes = __shfl_sync(0xffffffffu, outRes, src);
         if (lead) {
-          inRes = real ? prmt(wa, 0u, sel_one(s4)) : kPadPair;
-          if (from_strip) {
-            const uint2 v = gslot[s];
-            inH = (W)v.x;
-            inF = (W)v.y;
-          } else {
-            inH = 0;
-            inF = 0;
-          }
+          // (the ring holds the pad code past the target's end, the slot the
+          // top boundary where no band lies above)
+          inRes = prmt(wa, 0u, sel_one(s4));
+          const uint2 v = gslot[s];
+          inH = (W)v.x;
+          inF = (W)v.y;
         }
         column_step<R, kFormInt32>(st, prow, stride, inRes, inH, inF, cs, S, outH, outF);
         outRes = inRes;
@@ -217,6 +217,10 @@ __device__ __forceinline__ bool band_pass(const uint8_t *__restrict__ pch, const
     if (prev && blk + 1 < nreal) {
       land((blk + 1) & 1);
       if (!failed && blk + 2 < nreal) load();
+    } else if (prev && blk + 1 < nblk) {
+      // the two padding blocks after the last real one: top boundary again
+      if (lane < kColBlock) rgb[((blk + 1) & 1) * kColBlock + lane] = make_uint2(0u, 0u);
+      __syncwarp();
     }
   }
   if (lead) cp_async_wait<0>();
