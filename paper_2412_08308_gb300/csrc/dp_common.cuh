@@ -141,6 +141,37 @@ __device__ __forceinline__ void word_rows(uint32_t hd0, const uint32_t (&p)[N], 
 template <int FORM>
 using Word = typename std::conditional<FORM != kFormInt32, uint32_t, int32_t>::type;
 
+// N rows [R0, R0 + N) of one column in int32, Algorithm 1 statement by
+// statement.  hul is H of the row above R0 at the previous column, (hu, fu) H
+// and F of that row at this column (replaced by those of row R0 + N - 1); pb
+// the rows' profile bytes, four per word; E and Hl hold the previous column's
+// E and H per row and are updated in place; S keeps the running best.
+template <int R0, int N, int R>
+__device__ __forceinline__ void int_rows(int32_t hul, const uint32_t (&pb)[N / 4], int32_t (&E)[R], int32_t (&Hl)[R],
+                                         int32_t &hu, int32_t &fu, int32_t &S, const Consts &cs) {
+  static_assert(R0 + N <= R && N % 4 == 0, "rows in range, whole profile words");
+#pragma unroll
+  for (int r = 0; r < N; ++r) {
+    const int32_t sm = (int32_t)prmt(pb[r >> 2], 0u, sel_sext(r & 3));
+    const int32_t e1 = E[R0 + r] - cs.ge;
+    const int32_t e2 = Hl[R0 + r] - cs.go;
+    const int32_t e = max(e1, e2);
+    const int32_t f1 = fu - cs.ge;
+    const int32_t f2 = hu - cs.go;
+    const int32_t f = max(f1, f2);
+    int32_t h = hul + sm;
+    h = max(h, e);
+    h = max(h, f);
+    h = max(h, 0);
+    S = max(S, h);
+    hul = Hl[R0 + r];
+    Hl[R0 + r] = h;
+    E[R0 + r] = e;
+    hu = h;
+    fu = f;
+  }
+}
+
 // Per-lane DP state of R rows.
 template <int R, int FORM>
 struct LaneState {
@@ -189,14 +220,9 @@ __device__ __forceinline__ void column_step(LaneState<R, FORM> &st, const uint8_
     S = (W)s;
     outH = st.Hl[R - 1];
     outF = (W)f;
-    st.hdiag = inH;
-    return;
-  }
-  constexpr bool PACKED = FORM == kFormPacked;
-  uint32_t pa[R / 4];
-  load_prof<R>(prow + (res & 0xffu) * stride, pa);
-  if constexpr (PACKED) {
-    uint32_t pb[R / 4];
+  } else if constexpr (FORM == kFormPacked) {
+    uint32_t pa[R / 4], pb[R / 4];
+    load_prof<R>(prow + (res & 0xffu) * stride, pa);
     load_prof<R>(prow + (res >> 16) * stride, pb);
     uint32_t pw[R];
 #pragma unroll
@@ -207,28 +233,11 @@ __device__ __forceinline__ void column_step(LaneState<R, FORM> &st, const uint8_
     outH = st.Hl[R - 1];
     outF = (W)f;
   } else {
-    // Algorithm 1, statement by statement.
-    int32_t hul = (int32_t)st.hdiag, hu = (int32_t)inH, fu = (int32_t)inF;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int32_t sm = (int32_t)prmt(pa[r >> 2], 0u, sel_sext(r & 3));
-      const int32_t e1 = (int32_t)st.E[r] - cs.ge;
-      const int32_t e2 = (int32_t)st.Hl[r] - cs.go;
-      const int32_t e = max(e1, e2);
-      const int32_t f1 = fu - cs.ge;
-      const int32_t f2 = hu - cs.go;
-      const int32_t f = max(f1, f2);
-      int32_t h = hul + sm;
-      h = max(h, e);
-      h = max(h, f);
-      h = max(h, 0);
-      S = (W)max((int32_t)S, h);
-      hul = (int32_t)st.Hl[r];
-      st.Hl[r] = (W)h;
-      st.E[r] = (W)e;
-      hu = h;
-      fu = f;
-    }
+    uint32_t pa[R / 4];
+    load_prof<R>(prow + (res & 0xffu) * stride, pa);
+    int32_t hu = inH, fu = inF, s = S;
+    int_rows<0, R>(st.hdiag, pa, st.E, st.Hl, hu, fu, s, cs);
+    S = (W)s;
     outH = (W)hu;
     outF = (W)fu;
   }
@@ -285,6 +294,38 @@ __device__ __forceinline__ void column_step_split(LaneState<R, FORM> &st, uint32
   S = s;
   midF = f;
   hdiagB = diagB_next;
+  st.hdiag = inH;
+}
+
+// int32 form with split lanes (the pair-band kernel): rows [0, R/2) at column
+// c, rows [R/2, R) at column c - 1.  The upper half's last row (H, F) of the
+// step before (midH, midF) and its H of the step before that (hdiagB) feed
+// the lower half; the lane passes on the lower half's last row, of column
+// c - 1.  resA / resB: the residue code of column c / c - 1.
+template <int R>
+__device__ __forceinline__ void column_step_split_int(LaneState<R, kFormInt32> &st, int32_t &hdiagB, int32_t &midH,
+                                                      int32_t &midF, const uint8_t *prow, int stride, uint32_t resA,
+                                                      uint32_t resB, int32_t inH, int32_t inF, const Consts &cs,
+                                                      int32_t &S, int32_t &S2, int32_t &outH, int32_t &outF) {
+  static_assert(R % 8 == 0, "halves of whole profile words");
+  constexpr int H2 = R / 2;
+  uint32_t pa[H2 / 4], pb[H2 / 4];
+  load_prof_at<H2, 0>(prow + (resA & 0xffu) * stride, pa);
+  load_prof_at<H2, H2>(prow + (resB & 0xffu) * stride, pb);
+  // lower half first in program order (its inputs are ready), then the upper
+  int32_t hu = midH, fu = midF, s2 = S2;
+  int_rows<H2, H2>(hdiagB, pb, st.E, st.Hl, hu, fu, s2, cs);
+  outH = hu;
+  outF = fu;
+  S2 = s2;
+  hdiagB = midH;
+  hu = inH;
+  fu = inF;
+  int32_t s = S;
+  int_rows<0, H2>(st.hdiag, pa, st.E, st.Hl, hu, fu, s, cs);
+  S = s;
+  midH = hu;
+  midF = fu;
   st.hdiag = inH;
 }
 

@@ -36,6 +36,12 @@ namespace swgb {
 namespace {
 
 constexpr int kPairThreads = 512;  // at most 16 warps per CTA, one band each
+// Split lanes (column_step_split_int): two half-chains per lane, lanes two
+// columns apart, so a band's last lane trails its first by 63 columns.
+template <int R>
+constexpr bool kBandSplit = R % 8 == 0;
+template <int R>
+constexpr int kBandLag = kBandSplit<R> ? 2 * 32 - 1 : 32 - 1;
 constexpr int kBandRingBytes = 320;  // residues: 2 slots x 32 B; boundary: 2 slots x 16 x 8 B
 
 struct BandIO {
@@ -56,6 +62,8 @@ __device__ __forceinline__ uint32_t band_gen(int b, int nslots) { return ((uint3
 // of block blk + 2 at the end of block blk and check their tags at the end of
 // block blk + 1 (loading again until they are fresh), then unpack them into
 // the shared-memory slot lane 0 reads.  Lane 31 stores one entry per column.
+// With split lanes each lane runs two half-chains a column apart (see
+// column_step_split_int).
 // Returns false when a wait expired.
 template <int R>
 __device__ __forceinline__ bool band_pass(const uint8_t *__restrict__ pch, const int stride, const int lane,
@@ -67,6 +75,9 @@ __device__ __forceinline__ bool band_pass(const uint8_t *__restrict__ pch, const
   lane_reset(st, cs);
   W outH = 0, outF = 0;
   uint32_t outRes = kPadPair;
+  // split lanes: the lower half's residue, diagonal H, incoming H and F, best
+  uint32_t prevRes = kPadPair;
+  int32_t hdiagB = 0, midH = 0, midF = 0, S2 = 0;
   const int src = lane > 0 ? lane - 1 : lane;
   const bool lead = lane == 0;
   const bool tail = lane == 31 && next;
@@ -159,7 +170,7 @@ __device__ __forceinline__ bool band_pass(const uint8_t *__restrict__ pch, const
   for (int blk = 0; blk < nblk && !failed; ++blk) {
     if (tail) {
       // room in this band's ring for the columns this block writes
-      const int jmax = min(blk * kColBlock + kColBlock - 1 - 31, npad - 1);
+      const int jmax = min(blk * kColBlock + kColBlock - 1 - kBandLag<R>, npad - 1);
       const int need = jmax + 1 - x.window;
       if (jmax >= 0 && seen_cons < need) {
         seen_cons = wait_flag_value(x.cons_out, need, kLongWaitBudgetCycles);
@@ -194,10 +205,17 @@ __device__ __forceinline__ bool band_pass(const uint8_t *__restrict__ pch, const
           inH = (W)v.x;
           inF = (W)v.y;
         }
-        column_step<R, kFormInt32>(st, prow, stride, inRes, inH, inF, cs, S, outH, outF);
-        outRes = inRes;
+        if constexpr (kBandSplit<R>) {
+          column_step_split_int<R>(st, hdiagB, midH, midF, prow, stride, inRes, prevRes, inH, inF, cs, S, S2, outH,
+                                   outF);
+          outRes = prevRes;
+          prevRes = inRes;
+        } else {
+          column_step<R, kFormInt32>(st, prow, stride, inRes, inH, inF, cs, S, outH, outF);
+          outRes = inRes;
+        }
         if (tail) {
-          const int j = t - 31;
+          const int j = t - kBandLag<R>;
           if (j >= 0 && j < npad) {
             const uint32_t lo = (uint32_t)outH | (wlap << 31);
             const uint32_t hi = (uint32_t)(outF + cs.go) | gen_bit;
@@ -218,12 +236,13 @@ __device__ __forceinline__ bool band_pass(const uint8_t *__restrict__ pch, const
       land((blk + 1) & 1);
       if (!failed && blk + 2 < nreal) load();
     } else if (prev && blk + 1 < nblk) {
-      // the two padding blocks after the last real one: top boundary again
+      // the padding blocks after the last real one: top boundary again
       if (lane < kColBlock) rgb[((blk + 1) & 1) * kColBlock + lane] = make_uint2(0u, 0u);
       __syncwarp();
     }
   }
   if (lead) cp_async_wait<0>();
+  S = max(S, S2);
   return !failed;
 }
 
@@ -235,7 +254,7 @@ __global__ void __launch_bounds__(kPairThreads, 1) pair_band_kernel(const PairBa
   uint8_t *pbuf = smem + (size_t)warp * (a.pbuf_bytes + kBandRingBytes);
   uint8_t *ring = pbuf + a.pbuf_bytes;
   const Consts cs = make_consts(a.sc);
-  const int nblk = (a.npad + 31 + kColBlock - 1) / kColBlock;
+  const int nblk = (a.npad + kBandLag<R> + kColBlock - 1) / kColBlock;
   int32_t S = 0;
   // global warp g = warp * grid + CTA: bands spread over the SMs first
   for (int b = warp * gridDim.x + blockIdx.x; b < a.nbands; b += gridDim.x * nw) {
