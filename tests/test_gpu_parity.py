@@ -200,11 +200,13 @@ def test_query_pairs_only_where_no_lane_can_overflow(api):
     assert info[3] == info_off[3] + 2
 
 
-@pytest.mark.parametrize("R,L", [(4, 0), (8, 0), (24, 0), (4, 4), (12, 7)])
+@pytest.mark.parametrize("R,L", [(4, 0), (8, 0), (24, 0), (4, 4), (12, 7), (16, 0), (16, 32), (24, 32), (8, 5)])
 def test_query_pairs_tiles(api, R, L):
     # tracks at several rows-per-lane instances; with 4 x 4 rows per chunk a
     # track switches queries many times (restarting its half from the matrix
-    # top boundary) and queries span up to 57 chunks
+    # top boundary) and queries span up to 57 chunks.  R = 8, 16, 24 run split
+    # lanes (two half-chains a column apart; 32 lanes: a 63-column chain lag),
+    # R = 4 and 12 one chain per lane
     db, _ = _ragged(40 + R + L, 257, 3, 10)
     rng = np.random.Generator(np.random.PCG64(R + L))
     q = from_list([rng.integers(0, 20, size=n).astype(np.uint8) for n in (900, 880, 333, 300, 5, 4, 17, 16, 1)])
