@@ -1,5 +1,6 @@
-// Cell arithmetic shared by the inter-task and intra-task kernels: one column
-// step of R query rows owned by one lane (Sec. 2.2 Eqs. 1-3).
+// Cell arithmetic shared by the inter-task, intra-task and pair-band kernels:
+// one column step of R query rows owned by one lane (Sec. 2.2 Eqs. 1-3), or,
+// with split lanes, the lane's two halves of R/2 rows a column apart.
 //
 // int32 form: Algorithm 1's statements, one cell per lane op.
 // packed form: two cells per 32-bit word, each 16-bit half a signed cell value.
