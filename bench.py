@@ -175,11 +175,38 @@ def dp_kernel_traffic():
     return rec.get("dram_bytes_per_launch")
 
 
+def strip_c_comments(text):
+    """C/C++ source without comments and blank lines (string and character
+    literals kept), so that documentation edits leave the hash unchanged."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            while i < n and text[i] != "\n":
+                i += 1
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    lines = ("".join(out)).splitlines()
+    return "\n".join(line.rstrip() for line in lines if line.strip())
+
+
 def dp_kernel_source_sha1():
-    """SHA-1 over the sources that define the inter-task DP kernel."""
+    """SHA-1 over the code (comments removed) of the sources that define the
+    inter-task DP kernel."""
     h = hashlib.sha1()
     for f in ("k_inter.cu", "dp_common.cuh", "internal.h", "devutil.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2412_08308_gb300", "csrc", f), "rb").read())
+        text = open(os.path.join(ROOT, "paper_2412_08308_gb300", "csrc", f), encoding="utf-8").read()
+        h.update(strip_c_comments(text).encode())
     return h.hexdigest()
 
 
