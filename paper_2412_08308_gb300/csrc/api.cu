@@ -83,6 +83,10 @@ struct sw_db {
   std::vector<int32_t> h_len;   // true lengths in sorted order
   std::vector<int32_t> h_pos;   // sorted position of each sequence, caller order
   std::vector<int64_t> h_off;   // residue offsets in sorted order
+  // device [0, 1, ..., n - 1, n - 1]: the sorted positions of the database
+  // units (one sequence, or two consecutive ones in packed mode, the last
+  // repeated when n is odd), shared by every query batch
+  const int32_t *d_ident = nullptr;
 };
 
 struct sw_queries {
@@ -118,7 +122,7 @@ struct sw_queries {
   QDesc *d_qd = nullptr, *d_qdi = nullptr, *d_qdp = nullptr;
   TrackChunk *d_track = nullptr;
   Task *d_tasks = nullptr, *d_itasks = nullptr, *d_itasks32 = nullptr, *d_rtasks = nullptr, *d_ptasks = nullptr;
-  int32_t *d_units = nullptr, *d_ipos32 = nullptr, *d_upos = nullptr;
+  int32_t *d_ipos32 = nullptr, *d_upos = nullptr;
   uint8_t *d_prof = nullptr;
   int64_t prof_bytes = 0;
   uint2 *d_gbuf = nullptr, *d_igbuf = nullptr;
@@ -243,7 +247,8 @@ int sw_db_prepare(const uint8_t *residues, const int64_t *offsets, int64_t n_seq
   const size_t b_res = round_up((int64_t)packed.size(), 256);
   const size_t b_off = round_up(8 * std::max<int64_t>(n_seqs, 1), 256);
   const size_t b_i32 = round_up(4 * std::max<int64_t>(n_seqs, 1), 256);
-  db->bytes = b_res + b_off + 3 * b_i32;
+  const size_t b_ident = round_up(4 * (n_seqs + 1), 256);
+  db->bytes = b_res + b_off + 3 * b_i32 + b_ident;
   cudaError_t e = cudaMalloc(&db->block, db->bytes);
   if (e != cudaSuccess) {
     delete db;
@@ -256,6 +261,9 @@ int sw_db_prepare(const uint8_t *residues, const int64_t *offsets, int64_t n_seq
   db->view.len = (const int32_t *)(p + b_res + b_off + b_i32);
   db->view.perm = (const int32_t *)(p + b_res + b_off + 2 * b_i32);
   db->view.n = n_seqs;
+  db->d_ident = (const int32_t *)(p + b_res + b_off + 3 * b_i32);
+  std::vector<int32_t> ident((size_t)n_seqs + 1);
+  for (int64_t k = 0; k <= n_seqs; ++k) ident[k] = (int32_t)std::max<int64_t>(0, std::min<int64_t>(k, n_seqs - 1));
   e = cudaMemcpyAsync((void *)db->view.res, packed.data(), packed.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && n_seqs) {
     e = cudaMemcpyAsync((void *)db->view.off, off.data(), 8 * n_seqs, cudaMemcpyHostToDevice, s);
@@ -263,6 +271,8 @@ int sw_db_prepare(const uint8_t *residues, const int64_t *offsets, int64_t n_seq
     if (e == cudaSuccess) e = cudaMemcpyAsync((void *)db->view.len, slen.data(), 4 * n_seqs, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync((void *)db->view.perm, order.data(), 4 * n_seqs, cudaMemcpyHostToDevice, s);
   }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync((void *)db->d_ident, ident.data(), 4 * ident.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     cudaFree(db->block);
@@ -346,17 +356,11 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   const std::vector<int32_t> &npad = db->h_npad;
 
   // --- units (sorted positions); a unit is long when its first (longest) sequence reaches the cutover
+  // (unit u: sorted positions 2u and min(2u + 1, n - 1) in packed mode, u in
+  // int32 mode; the database's identity array holds them on the device)
   Q->n_units = packed ? (n + 1) / 2 : n;
-  std::vector<int32_t> units(std::max<int64_t>(1, packed ? 2 * Q->n_units : n));
-  if (packed) {
-    for (int64_t u = 0; u < Q->n_units; ++u) {
-      units[2 * u] = (int32_t)(2 * u);
-      units[2 * u + 1] = (int32_t)std::min<int64_t>(2 * u + 1, n - 1);
-    }
-  } else {
-    for (int64_t u = 0; u < n; ++u) units[u] = (int32_t)u;
-  }
-  auto unit_len = [&](int64_t u) { return npad[units[packed ? 2 * u : u]]; };
+  auto unit_seq = [&](int64_t i) { return (int32_t)std::min<int64_t>(i, n - 1); };
+  auto unit_len = [&](int64_t u) { return npad[unit_seq(packed ? 2 * u : u)]; };
   int64_t n_long = 0;
   while (n_long < Q->n_units && unit_len(n_long) >= cutover) ++n_long;
   Q->n_long = n_long;
@@ -696,8 +700,8 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
         twi.push_back({Task{(int32_t)q, (int32_t)u, 1, 0}, w});
         continue;
       }
-      const int32_t a = units[packed ? 2 * u : u];
-      const int32_t b = packed ? units[2 * u + 1] : a;
+      const int32_t a = unit_seq(packed ? 2 * u : u);
+      const int32_t b = packed ? unit_seq(2 * u + 1) : a;
       twi32.push_back({Task{(int32_t)q, (int32_t)ipos32.size(), 1, 0}, 2 * w});
       ipos32.push_back(a);
       if (b != a) {
@@ -769,8 +773,6 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   const size_t b_qdp = round_up(sizeof(QDesc) * std::max<int64_t>(Q->npairs, 1), 256);
   const size_t b_track = round_up(sizeof(TrackChunk) * std::max<int64_t>((int64_t)Q->track.size(), 1), 256);
   const size_t b_ptasks = round_up(sizeof(Task) * std::max<int64_t>(Q->n_ptasks, 1), 256);
-  const size_t b_upos = round_up(4 * std::max<int64_t>(Q->npairs ? Q->n_single : 0, 1), 256);
-  const size_t b_units = round_up(4 * (int64_t)units.size(), 256);
   const size_t b_prof = round_up(Q->prof_bytes, 256);
   const size_t b_gbuf = round_up((int64_t)gslots * warps * 8 * (int64_t)Q->gbuf_stride * 8, 256);
   // (two intra-task launches at once, packed and int32, each with its strips)
@@ -779,8 +781,8 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   const size_t b_words = round_up(4 * (12 + 2 * nqm), 256);  // zeroed words + 3 constants
   const size_t b_flag = Q->inter_may_flag ? round_up(4 * nqm * std::max<int64_t>(n, 1), 256) : 0;
   const size_t b_iflag = packed ? round_up(4 * nqm * Q->long_stride, 256) : 0;
-  Q->bytes = b_qres + b_sub + 2 * b_qd + b_tasks + b_itasks + b_itasks32 + b_ipos32 + b_rtasks + b_units + b_prof +
-             b_gbuf + b_igbuf + b_words + b_flag + b_iflag + b_qdp + b_ptasks + b_upos + b_track;
+  Q->bytes = b_qres + b_sub + 2 * b_qd + b_tasks + b_itasks + b_itasks32 + b_ipos32 + b_rtasks + b_prof +
+             b_gbuf + b_igbuf + b_words + b_flag + b_iflag + b_qdp + b_ptasks + b_track;
   cudaError_t e = cudaMallocAsync(&Q->block, Q->bytes, s);
   if (e != cudaSuccess) {
     delete Q;
@@ -801,7 +803,6 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   Q->d_itasks32 = (Task *)take(b_itasks32);
   Q->d_ipos32 = (int32_t *)take(b_ipos32);
   Q->d_rtasks = (Task *)take(b_rtasks);
-  Q->d_units = (int32_t *)take(b_units);
   Q->d_prof = take(b_prof);
   Q->d_gbuf = (uint2 *)take(b_gbuf);
   Q->d_igbuf = (uint2 *)take(b_igbuf);
@@ -811,11 +812,9 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   Q->d_qdp = (QDesc *)take(b_qdp);
   Q->d_track = (TrackChunk *)take(b_track);
   Q->d_ptasks = (Task *)take(b_ptasks);
-  Q->d_upos = (int32_t *)take(b_upos);
+  Q->d_upos = const_cast<int32_t *>(db->d_ident) + s0;  // the short sequences, in sorted order
 
   std::vector<Task> tasks(Q->n_tasks), itasks(Q->n_itasks), itasks32(Q->n_itasks32), ptasks(Q->n_ptasks);
-  std::vector<int32_t> upos(Q->npairs ? Q->n_single : 0);
-  for (int64_t i = 0; i < (int64_t)upos.size(); ++i) upos[i] = (int32_t)(s0 + i);
   for (int64_t i = 0; i < Q->n_ptasks; ++i) ptasks[i] = twp[i].t;
   for (int64_t i = 0; i < Q->n_tasks; ++i) tasks[i] = tw[i].t;
   for (int64_t i = 0; i < Q->n_itasks; ++i) itasks[i] = twi[i].t;
@@ -825,7 +824,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   Q->h2d_bytes = q_offsets[n_queries] + 400 + 2 * (int64_t)sizeof(QDesc) * n_queries +
                  (int64_t)sizeof(QDesc) * Q->npairs + (int64_t)sizeof(TrackChunk) * (int64_t)Q->track.size() +
                  (int64_t)sizeof(Task) * (Q->n_tasks + Q->n_itasks + Q->n_itasks32 + Q->n_ptasks) +
-                 4 * (int64_t)units.size() + 4 * (int64_t)ipos32.size() + 4 * (int64_t)upos.size() + 16;
+                 4 * (int64_t)ipos32.size() + 16;
   e = cudaSuccess;
   if (q_offsets[n_queries] > 0)
     e = cudaMemcpyAsync(Q->d_qres, queries, q_offsets[n_queries], cudaMemcpyHostToDevice, s);
@@ -850,10 +849,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
                           s);
     if (e == cudaSuccess && Q->n_ptasks)
       e = cudaMemcpyAsync(Q->d_ptasks, ptasks.data(), sizeof(Task) * Q->n_ptasks, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && !upos.empty())
-      e = cudaMemcpyAsync(Q->d_upos, upos.data(), 4 * upos.size(), cudaMemcpyHostToDevice, s);
   }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(Q->d_units, units.data(), 4 * units.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(Q->d_words, 0, b_words, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(Q->d_words + Q->zero_words(), consts, sizeof consts, cudaMemcpyHostToDevice, s);
@@ -906,7 +902,7 @@ int sw_search_prepared(const sw_db *db, const sw_queries *Q, int32_t *scores_dev
 
   InterArgs a{};
   a.db = db->view;
-  a.unit_pos = Q->d_units;
+  a.unit_pos = db->d_ident;
   a.prof = Q->d_prof;
   a.out = scores_dev;
   a.out_stride = db->n;
