@@ -400,6 +400,8 @@ def run_ours(args, w):
 
     extras = {}
     if not args.no_extras and rank == 0:
+        # alignments of each query's best hits (sw_traceback)
+        extras["traceback_top10"] = traceback_rate(api, db, q, out)
         # the plain int32 kernel (Algorithm 1 body) on the same workload
         pq32 = api.PreparedQueries(db, q.residues, q.offsets, BLOSUM62, 10, 2, "int32")
         pq32.search(out)
@@ -482,6 +484,28 @@ def run_ours(args, w):
     db.close()
     if pg is not None:
         pg.destroy_process_group()
+
+
+def traceback_rate(api, db, q, out, k=10):
+    """sw_traceback on each query's k best-scoring database sequences (the hits
+    a caller keeps), timed on the host around the call (uploads, kernels,
+    downloads); its rate counts the cells of the recomputed matrices.  Each
+    alignment's score must equal the search score of its pair."""
+    from workload.matrices import BLOSUM62
+
+    scores = out.cpu().numpy()
+    hits = []
+    for i in range(scores.shape[0]):
+        hits += [(i, int(t)) for t in np.argsort(-scores[i], kind="stable")[:k]]
+    qlen = np.diff(q.offsets)
+    cells = float(sum(int(qlen[a]) * int(db.lengths[b]) for a, b in hits))
+    api.traceback(db, q.residues, q.offsets, hits, BLOSUM62, 10, 2)  # warm-up
+    t0 = time.perf_counter()
+    res = api.traceback(db, q.residues, q.offsets, hits, BLOSUM62, 10, 2)
+    dt = time.perf_counter() - t0
+    same = all(int(r[0]) == int(scores[a, b]) for r, (a, b) in zip(res, hits))
+    return {"hits": len(hits), "cells": cells, "ms": round(1e3 * dt, 2), "gcups": round(cells / dt / 1e9, 1),
+            "scores_match_search": same}
 
 
 def dna_pair_gcups(name, reps=2):

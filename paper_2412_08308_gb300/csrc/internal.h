@@ -135,14 +135,14 @@ struct TraceHit {
   int64_t qoff;       // query residues in qres
   int64_t toff;       // target residues in tres (the database's sorted, padded residues)
   int64_t dir_off;    // bytes into dirs: mrow * npad / 2, column-major nibbles (row i of column j at j * mrow + i)
-  int64_t strip_off;  // uint2 entries into strips: npad (chunk boundary rows)
+  int64_t strip_off;  // uint2 entries into strips: npad (bottom rows passed from the last warp to the first)
   int64_t ops_off;    // bytes into ops: m + n
   int32_t m, n, npad, mrow;  // query and target lengths, padded target length, rows padded to whole chunks
 };
 struct TraceResult {
   int32_t score, end_i, end_j;  // best score and its cell (1-based row, column; first in row-major order)
   int32_t begin_i, begin_j;     // the alignment covers rows begin_i+1 .. end_i, columns begin_j+1 .. end_j
-  int32_t n_ops;
+  int32_t n_ops;                // -1: the fill gave up on a bounded wait
 };
 struct TraceArgs {
   const uint8_t *qres, *tres;
@@ -156,7 +156,9 @@ struct TraceArgs {
   Scoring sc;
 };
 int trace_rows_per_chunk();
-cudaError_t launch_trace(const TraceArgs &a, cudaStream_t s);
+int trace_warps(int max_chunks);  // warps per CTA of the fill: chunks of one hit in flight
+size_t trace_smem_bytes(int warps);
+cudaError_t launch_trace(const TraceArgs &a, int warps, cudaStream_t s);
 
 // launchers (k_inter.cu)
 int inter_threads();

@@ -66,10 +66,11 @@ extern "C" int sw_traceback(const sw_db *db, const uint8_t *queries, const int64
     return tr_fail(SW_EINVAL, "sw_traceback: gap penalties out of range (%lld, %lld)", gap_open, gap_extend);
   const int64_t ndb = db_view(db).n;
 
-  // per-hit layout: direction nibbles, boundary strip, operations
+  // per-hit layout: direction nibbles, operations
   const int chunk = trace_rows_per_chunk();
   std::vector<TraceHit> th((size_t)n_hits);
   int64_t dir_bytes = 0, strip_entries = 0, ops_bytes = 0;
+  int max_chunks = 1;
   for (int64_t h = 0; h < n_hits; ++h) {
     const int32_t qi = hits[h].query, ti = hits[h].target;
     if (qi < 0 || qi >= n_queries) return tr_fail(SW_EINVAL, "sw_traceback: hit %lld: query index %lld out of range", h, qi);
@@ -85,9 +86,10 @@ extern "C" int sw_traceback(const sw_db *db, const uint8_t *queries, const int64
     x.dir_off = dir_bytes;
     x.strip_off = strip_entries;
     x.ops_off = ops_bytes;
-    dir_bytes += tr_round_up((int64_t)x.mrow * x.npad / 2, 256);
     strip_entries += tr_round_up(x.npad, 32);
+    dir_bytes += tr_round_up((int64_t)x.mrow * x.npad / 2, 256);
     ops_bytes += (int64_t)x.m + x.n;
+    max_chunks = std::max(max_chunks, x.mrow / chunk);
   }
   if (ops_bytes > ops_capacity)
     return tr_fail(SW_EINVAL, "sw_traceback: ops buffer holds %lld bytes, the hits need %lld", ops_capacity,
@@ -97,8 +99,8 @@ extern "C" int sw_traceback(const sw_db *db, const uint8_t *queries, const int64
   const int64_t b_q = tr_round_up(std::max<int64_t>(q_offsets[n_queries], 1), 256);
   const int64_t b_sub = 512, b_hits = tr_round_up((int64_t)sizeof(TraceHit) * n_hits, 256);
   const int64_t b_res = tr_round_up((int64_t)sizeof(TraceResult) * n_hits, 256);
-  const int64_t b_strip = tr_round_up(strip_entries * (int64_t)sizeof(uint2), 256);
   const int64_t b_ops = tr_round_up(std::max<int64_t>(ops_bytes, 1), 256);
+  const int64_t b_strip = tr_round_up(strip_entries * (int64_t)sizeof(uint2), 256);
   const int64_t bytes = b_q + b_sub + b_hits + b_res + b_strip + b_ops + dir_bytes;
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && (size_t)bytes > free_b)
@@ -127,9 +129,9 @@ extern "C" int sw_traceback(const sw_db *db, const uint8_t *queries, const int64
   a.hits = d_hits;
   a.nhits = (int32_t)n_hits;
   a.dirs = d_dirs;
-  a.strips = d_strip;
   a.ops = d_ops;
   a.results = d_res;
+  a.strips = d_strip;
   a.sc.go = gap_open + gap_extend;
   a.sc.ge = gap_extend;
   a.sc.pad = std::min(0, smin);
@@ -140,12 +142,14 @@ extern "C" int sw_traceback(const sw_db *db, const uint8_t *queries, const int64
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_sub, submat, 400, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_hits, th.data(), sizeof(TraceHit) * n_hits, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return tr_cuda(e, "upload");
-  if ((e = launch_trace(a, s)) != cudaSuccess) return tr_cuda(e, "traceback kernels");
+  if ((e = launch_trace(a, trace_warps(max_chunks), s)) != cudaSuccess) return tr_cuda(e, "traceback kernels");
   std::vector<TraceResult> res((size_t)n_hits);
   e = cudaMemcpyAsync(res.data(), d_res, sizeof(TraceResult) * n_hits, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && ops_bytes > 0) e = cudaMemcpyAsync(ops, d_ops, ops_bytes, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return tr_cuda(e, "results");
+  for (int64_t h = 0; h < n_hits; ++h)
+    if (res[h].n_ops < 0) return tr_fail(SW_ETIMEOUT, "sw_traceback: hit %lld: a bounded device wait expired", h);
   for (int64_t h = 0; h < n_hits; ++h) {
     sw_alignment &o = out[h];
     o.score = res[h].score;

@@ -81,12 +81,26 @@ def test_dna_hits_with_indels(api, go, ge):
 
 
 def test_many_hits_and_repeats(api):
-    # 200 hits in one call (one warp each), the same pair several times
+    # 200 hits in one call (one CTA each), the same pair several times
     rng = np.random.Generator(np.random.PCG64(93))
     seqs = [rng.integers(0, 20, size=int(rng.integers(1, 300))).astype(np.uint8) for _ in range(50)]
     qs = [rng.integers(0, 20, size=int(rng.integers(1, 300))).astype(np.uint8) for _ in range(8)]
     hits = [(int(rng.integers(0, 8)), int(rng.integers(0, 50))) for _ in range(197)] + [(1, 2)] * 3
     _check(api, from_list(seqs), from_list(qs), hits, BLOSUM62, 10, 2)
+
+
+def test_long_queries_several_rounds(api):
+    # queries of 18 and 9 chunks of 512 rows: 8 warps per hit take the chunks
+    # in rounds, the last warp's rows passing to the first through the strip
+    rng = np.random.Generator(np.random.PCG64(95))
+    q0 = rng.integers(0, 20, size=9000).astype(np.uint8)
+    q1 = rng.integers(0, 20, size=4100).astype(np.uint8)
+    t0 = np.concatenate([rng.integers(0, 20, size=100).astype(np.uint8), q0[2000:3200], q0[6000:6300]])
+    t0[300:900:7] = (t0[300:900:7] + 3) % 20
+    t1 = np.concatenate([q1[3500:4100], rng.integers(0, 20, size=50).astype(np.uint8), q1[:400]])
+    t2 = rng.integers(0, 20, size=777).astype(np.uint8)
+    _check(api, from_list([t0, t1, t2]), from_list([q0, q1]), [(0, 0), (0, 1), (0, 2), (1, 1), (1, 0), (1, 2)],
+           BLOSUM62, 10, 2)
 
 
 def test_invalid_hits(api):
