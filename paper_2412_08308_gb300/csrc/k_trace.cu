@@ -38,6 +38,9 @@ struct TraceShared {
   int32_t bs[kTraceWarpsMax], bi[kTraceWarpsMax], bj[kTraceWarpsMax];
 };
 
+// shared memory: the counters above, then per warp a profile and a ring
+constexpr size_t kTraceHead = (sizeof(TraceShared) + 127) / 128 * 128;
+
 __device__ __forceinline__ bool earlier(int32_t s, int32_t i, int32_t j, int32_t bs, int32_t bi, int32_t bj) {
   // better score, or the same score at a cell earlier in row-major order
   return s > bs || (s == bs && (i < bi || (i == bi && j < bj)));
@@ -62,8 +65,8 @@ __global__ void __launch_bounds__(32 * kTraceWarpsMax) trace_fill_kernel(const T
   extern __shared__ __align__(16) uint8_t smem[];
   TraceShared *sh = reinterpret_cast<TraceShared *>(smem);
   const int W = blockDim.x >> 5;
-  uint4 *prof_all = reinterpret_cast<uint4 *>(smem + 256);                             // [warp][21][32]
-  uint2 *rings = reinterpret_cast<uint2 *>(smem + 256 + W * trace_prof_bytes());         // [warp][ring]
+  uint4 *prof_all = reinterpret_cast<uint4 *>(smem + kTraceHead);                      // [warp][21][32]
+  uint2 *rings = reinterpret_cast<uint2 *>(smem + kTraceHead + W * trace_prof_bytes());  // [warp][ring]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const TraceHit hit = a.hits[blockIdx.x];
   if (threadIdx.x < kTraceWarpsMax) {
@@ -298,7 +301,7 @@ int trace_rows_per_chunk() { return kTraceChunk; }
 
 int trace_warps(int max_chunks) { return std::max(1, std::min(kTraceWarpsMax, max_chunks)); }
 
-size_t trace_smem_bytes(int warps) { return 256 + (size_t)warps * (trace_prof_bytes() + trace_ring_bytes()); }
+size_t trace_smem_bytes(int warps) { return kTraceHead + (size_t)warps * (trace_prof_bytes() + trace_ring_bytes()); }
 
 cudaError_t launch_trace(const TraceArgs &a, int warps, cudaStream_t s) {
   if (a.nhits <= 0) return cudaSuccess;
