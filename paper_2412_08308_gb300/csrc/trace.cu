@@ -102,10 +102,6 @@ extern "C" int sw_traceback(const sw_db *db, const uint8_t *queries, const int64
   const int64_t b_ops = tr_round_up(std::max<int64_t>(ops_bytes, 1), 256);
   const int64_t b_strip = tr_round_up(strip_entries * (int64_t)sizeof(uint2), 256);
   const int64_t bytes = b_q + b_sub + b_hits + b_res + b_strip + b_ops + dir_bytes;
-  size_t free_b = 0, total_b = 0;
-  if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && (size_t)bytes > free_b)
-    return tr_fail(SW_ENOMEM, "sw_traceback: needs %lld bytes of device memory, %lld free", bytes,
-                   (long long)free_b);
   cudaStream_t s = (cudaStream_t)stream;
   TraceScratch sc;
   sc.s = s;
