@@ -287,10 +287,11 @@ int sw_align_pair(const uint8_t *query, int64_t m, const uint8_t *target, int64_
  * the path that produced it is the alignment).  The paper's search reports
  * scores only; this recovers the alignments of the hits a caller keeps.
  *
- * One warp per hit recomputes the pair's matrix in int32 and records 4 bits
- * per cell (where H came from; whether E and F extend a gap); one thread per
- * hit walks them back from the first cell, in row-major order, that holds the
- * score.  Device memory: about m * n / 2 bytes per hit (held during the call).
+ * One CTA per hit recomputes the pair's matrix in int32, its warps taking
+ * the query's 512-row chunks as a pipeline, and records 4 bits per cell (where
+ * H came from; whether E and F extend a gap); one thread per hit walks them
+ * back from the first cell, in row-major order, that holds the score.  Device
+ * memory: about m * n / 2 bytes per hit (held during the call).
  *
  *   db                    a prepared database
  *   queries, q_offsets, n_queries   host pointers, as sw_queries_prepare
@@ -308,7 +309,8 @@ int sw_align_pair(const uint8_t *query, int64_t m, const uint8_t *target, int64_
  * the substitution scores of its 'M' pairs minus gap_open + k * gap_extend per
  * maximal run of k 'I' or k 'D'; that is out[h].score.  A score of 0 gives an
  * empty alignment.
- * Errors: SW_EINVAL (bad indices, small ops buffer), SW_ENOMEM, SW_ECUDA.
+ * Errors: SW_EINVAL (bad indices, small ops buffer), SW_ENOMEM, SW_ECUDA,
+ * SW_ETIMEOUT (a bounded wait between the warps of a hit expired).
  */
 typedef struct sw_hit {
   int32_t query;   /* index into the query batch */
