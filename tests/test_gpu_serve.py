@@ -58,3 +58,21 @@ def test_results_same_alone_and_in_the_mix(api, mode):
     st = srv.latency_stats()
     assert st["requests"] == len(qs) and st["p99_ms"] >= st["p50_ms"] > 0
     db.close()
+
+
+def test_sharded_database_shards_on_one_gpu(api):
+    # every rank's shard of a 3-way split, searched on this GPU one after the
+    # other and put back in caller order, equals the whole search
+    from paper_2412_08308_gb300.shard import ShardedDatabase
+
+    db_s = random_sequences(75, 900, 300, 0.5, 20, 1000)
+    qs = random_sequences(76, 4, 300, 0.5, 30, 800)
+    full = np.zeros((len(qs), len(db_s)), dtype=np.int32)
+    for rank in range(3):
+        sh = ShardedDatabase(db_s.residues, db_s.offsets, rank, 3)
+        full[:, sh.mine] = api.search(sh.db, qs.residues, qs.offsets, BLOSUM62, 10, 2, "packed")
+        sh.close()
+    np.testing.assert_array_equal(full, oracle.scores(qs, db_s, BLOSUM62, 10, 2))
+    one = ShardedDatabase(db_s.residues, db_s.offsets, 0, 1)
+    np.testing.assert_array_equal(one.search(qs.residues, qs.offsets, BLOSUM62, 10, 2), full)
+    one.close()
