@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(32 * kTraceWarpsMax) trace_fill_kernel(const T
     uint32_t outRes = kPadCode;
     for (int blk = 0; blk < nsteps / kColBlock; ++blk) {
       const int col0 = blk * kColBlock;
-      // the band above has written this block's columns; room in this warp's ring
+      // the chunk above has written this block's columns; room in this warp's ring
       bool ok = true;
       if (lane == 0 && prev) ok &= trace_wait(&sh->prod[wprev], base_in + min(col0 + kColBlock, npad), vabort);
       if (lane == 31 && next && !strip_out) {
