@@ -330,6 +330,27 @@ int sw_traceback(const sw_db *db, const uint8_t *queries, const int64_t *q_offse
                  sw_alignment *out, uint8_t *ops, int64_t ops_capacity, void *stream);
 
 /* Message for the last failed call on this thread ("" if none). */
+/*
+ * sw_selftest_wait -- check that the library's bounded device waits give up.
+ * Every wait between warps or CTAs in the kernels (for a counter another warp
+ * raises, or an mbarrier phase a bulk copy completes) stops after a clock
+ * budget and reports SW_ETIMEOUT instead of hanging.  This runs one such wait
+ * against a condition nothing fulfils, on one GPU thread:
+ *
+ *   which          0: a progress counter that stays 0 (the pair-band
+ *                  kernel's waits for room), given budget_cycles cycles;
+ *                  1: an mbarrier phase that never completes (the profile
+ *                  waits), with the kernels' own budget of about one second
+ *   budget_cycles  clock cycles for which == 0, in (0, 2^32]; ignored for 1
+ *   status_out     host pointer: SW_ETIMEOUT when the wait gave up (the
+ *                  expected outcome), SW_OK if it was fulfilled
+ *   stream         stream for the work; the call returns when done
+ *
+ * No fault and no hang: the kernel returns after the budget and the context
+ * stays usable.  Errors: SW_EINVAL, SW_ENOMEM, SW_ECUDA.
+ */
+int sw_selftest_wait(int32_t which, int64_t budget_cycles, int32_t *status_out, void *stream);
+
 const char *sw_last_error(void);
 
 #ifdef __cplusplus

@@ -34,6 +34,7 @@ SIGNATURES = {
     "sw_search_noalloc": (ctypes.c_int, [_p, _p, _i64, _p, _i32, _i32, _p, _p]),
     "sw_align_pair": (ctypes.c_int, [_p, _i64, _p, _i64, _p, _i32, _i32, _p, _p, _p, _p]),
     "sw_traceback": (ctypes.c_int, [_p, _p, _p, _i64, _p, _i64, _p, _i32, _i32, _p, _p, _i64, _p]),
+    "sw_selftest_wait": (ctypes.c_int, [_i32, _i64, ctypes.POINTER(ctypes.c_int32), _p]),
     "sw_last_error": (ctypes.c_char_p, []),
 }
 
@@ -189,3 +190,8 @@ def sw_traceback(db, q_ptr, qoff_ptr, n_queries, hits, submat_ptr, gap_open, gap
                              stream))
     return out
 
+
+def sw_selftest_wait(which, budget_cycles, stream):
+    st = ctypes.c_int32(-1)
+    check(lib().sw_selftest_wait(int(which), int(budget_cycles), ctypes.byref(st), stream))
+    return st.value
