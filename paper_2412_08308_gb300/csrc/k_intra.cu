@@ -59,10 +59,13 @@ __device__ __forceinline__ void sweep_chunk(IntraShared *sh, const uint8_t *pbuf
                                             int32_t *status, const Consts &cs, Word<FORM> &S) {
   using W = Word<FORM>;
   constexpr bool PACKED = FORM != kFormInt32;
+  // split lanes (two half-chains a column apart): a warp's last lane trails
+  // its first by 63 columns instead of 31
+  constexpr int LAG = 2 * 32 - 1;
   const W H0 = (W)0;
   const W F0 = PACKED ? (W)cs.F0W : (W)0;
   volatile int32_t *vabort = &sh->abort;
-  const int nblk = (npad + 31 + kColBlock - 1) / kColBlock;
+  const int nblk = (npad + LAG + kColBlock - 1) / kColBlock;
   uint4 *ring_in = rings + (warp > 0 ? warp - 1 : 0) * kRing;
   uint4 *ring_out = rings + warp * kRing;
   const int g = warp * 32 + lane;
@@ -72,6 +75,9 @@ __device__ __forceinline__ void sweep_chunk(IntraShared *sh, const uint8_t *pbuf
   lane_reset(st, cs);
   W outH = H0, outF = F0;
   uint32_t outRes = kPadPair;
+  // split lanes: the lower half's residue, diagonal H, incoming H and F, best
+  uint32_t prevRes = kPadPair;
+  W hdiagB = H0, midH = H0, midF = F0, S2 = (W)0;
   const uint8_t *prow = pbuf + g * R;
   const bool first = warp == 0, last = warp == Wq - 1;
   // warp 0 reads residues and (after the first chunk) the boundary strip one
@@ -93,7 +99,7 @@ __device__ __forceinline__ void sweep_chunk(IntraShared *sh, const uint8_t *pbuf
     // consumer: the previous warp has written the columns this block reads
     if (lane == 0) {
       bool okw = true;
-      if (!last) okw &= wait_at_least(&sh->cons[warp + 1], col0 + kColBlock - 31 - kRing, vabort);
+      if (!last) okw &= wait_at_least(&sh->cons[warp + 1], col0 + kColBlock - LAG - kRing, vabort);
       if (!first) okw &= wait_at_least(&sh->prod[warp - 1], min(col0 + kColBlock, npad), vabort);
       if (!okw && !*vabort) {
         *vabort = 1;
@@ -143,10 +149,33 @@ __device__ __forceinline__ void sweep_chunk(IntraShared *sh, const uint8_t *pbuf
             inRes = v.z;
           }
         }
-        column_step<R, FORM>(st, prow, chunk_stride, inRes, inH, inF, cs, S, outH, outF);
-        outRes = inRes;
+        if constexpr (PACKED) {
+          uint32_t s = (uint32_t)S, s2 = (uint32_t)S2, hb = (uint32_t)hdiagB, mf = (uint32_t)midF, oh, of;
+          column_step_split<R, FORM>(st, hb, mf, prow, chunk_stride, inRes, prevRes, (uint32_t)inH, (uint32_t)inF,
+                                     cs, s, s2, oh, of, 0);
+          S = (W)s;
+          S2 = (W)s2;
+          hdiagB = (W)hb;
+          midF = (W)mf;
+          outH = (W)oh;
+          outF = (W)of;
+        } else {
+          int32_t s = (int32_t)S, s2 = (int32_t)S2, hb = (int32_t)hdiagB, mh = (int32_t)midH, mf = (int32_t)midF;
+          int32_t oh, of;
+          column_step_split_int<R>(st, hb, mh, mf, prow, chunk_stride, inRes, prevRes, (int32_t)inH, (int32_t)inF,
+                                   cs, s, s2, oh, of);
+          S = (W)s;
+          S2 = (W)s2;
+          hdiagB = (W)hb;
+          midH = (W)mh;
+          midF = (W)mf;
+          outH = (W)oh;
+          outF = (W)of;
+        }
+        outRes = prevRes;
+        prevRes = inRes;
         if (lane == 31) {
-          const int col = tau - 31;
+          const int col = tau - LAG;
           if (col >= 0 && col < npad) {
             if (!last) ring_out[col % kRing] = make_uint4((uint32_t)outH, (uint32_t)outF, outRes, 0u);
             else if (next) gb[col] = make_uint2((uint32_t)outH, (uint32_t)outF);
@@ -157,11 +186,12 @@ __device__ __forceinline__ void sweep_chunk(IntraShared *sh, const uint8_t *pbuf
     __syncwarp();
     if (lane == 31 && !last) {
       __threadfence_block();
-      const int written = min(max(0, col0 + kColBlock - 31), npad);
+      const int written = min(max(0, col0 + kColBlock - LAG), npad);
       *(volatile int32_t *)&sh->prod[warp] = written;
     }
     if (lane == 0 && !first) *(volatile int32_t *)&sh->cons[warp] = min(col0 + kColBlock, npad);
   }
+  S = score_max<FORM>(S, S2);
 }
 
 template <int R, bool PACKED>
