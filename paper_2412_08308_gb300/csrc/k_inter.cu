@@ -4,13 +4,16 @@
 // Work decomposition
 // ------------------
 // A *chain* of L lanes (4 <= L <= 32, several chains per warp) computes the
-// alignment matrix of one query against one database sequence (int32 form)
-// or against two sequences at once (packed form: two 16-bit cells per 32-bit
-// register).  Lane k of a chain owns R consecutive query rows of the current
-// *chunk* of L*R rows and sweeps the database columns; lane k works on column
-// t-k at step t, receiving the bottom row (H, F) of lane k-1 and the residue
-// code(s) through warp shuffles.  This is an anti-diagonal wavefront inside a
-// warp: cells on one anti-diagonal of lanes run in the same step.
+// alignment matrix of one query against one database sequence (int32 form),
+// against two sequences at once (packed form: two 16-bit cells per 32-bit
+// register), or of two queries against one sequence (query-pair form).  Lane
+// k of a chain owns R consecutive query rows of the current *chunk* of L*R
+// rows and sweeps the database columns; lane k works on column t-k at step t,
+// receiving the bottom row (H, F) of lane k-1 and the residue code(s) through
+// warp shuffles.  This is an anti-diagonal wavefront inside a warp: cells on
+// one anti-diagonal of lanes run in the same step.  In the 16-bit forms a
+// lane's rows are two half-chains a column apart (column_step_split), so lane
+// k works on column t-2k and its two halves' dependency chains interleave.
 //
 // The query is processed chunk by chunk.  All chains of a CTA work on the same
 // query and move from chunk to chunk together: the profile slice of the next
