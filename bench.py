@@ -39,12 +39,37 @@ SM_COUNT_FALLBACK = 152
 # The integer ALU pipe of an sm_103 SMSP accepts one warp instruction every
 # second cycle (ncu: a stream of IMNMX / VIMNMX / IADD / PRMT runs the ALU pipe
 # at ~99% with issue at ~51%), i.e. 64 lanes per clock per SM.  Every max of
-# the recurrences runs there; the DP kernels are bound by it.
+# the recurrences runs there; the DP kernels are bound by it.  The FMA pipe is
+# a second integer pipe of the same width (it takes the per-half 16x2 adds).
 ALU_LANES_PER_SM_CLK = 64
-# essential ALU-pipe (max) operations per cell: packed s16x2 = 5 per 32-bit
-# word of two cells (max with the zero floor, H, S, E, F); int32 = the 6 max
-# statements of Algorithm 1
-ALU_OPS_PER_CELL = {"packed": 2.5, "int32": 6.0}
+INT_PIPES = 2  # ALU + FMA: the lanes the paper's instruction model (Eqs. 4-6) can use for adds and maxima
+# Algorithmic integer operations per cell, the roofline's count:
+#  - packed s16x2: about 6 operations per 32-bit word of two cells (H - Go
+#    shared by E and F, the E and F max-adds, H_diag + SM, the three-way max
+#    with the zero floor, the running best), i.e. 3 per cell -- every one of
+#    them issues on the ALU pipe (adds fuse into the maxima that consume them);
+#  - int32: the 12 statements of Algorithm 1 (the paper's model, Eq. 6),
+#    against both integer pipes.
+# The maxima alone (the ALU pipe's irreducible work): 5 per word (2.5 per
+# cell) packed, 6 per cell int32.
+ALG_OPS_PER_CELL = {"packed": 3.0, "int32": 12.0}
+ALG_PIPES = {"packed": 1, "int32": INT_PIPES}
+ALU_MAX_OPS_PER_CELL = {"packed": 2.5, "int32": 6.0}
+
+
+def roofline_of(gcups, mode, n_sm, sm_mhz):
+    """ALU-pipe roofline fields of a DP kernel that ran at `gcups` (kernel time)."""
+    lanes = n_sm * ALU_LANES_PER_SM_CLK * sm_mhz * 1e6 / 1e9  # Gop/s of one integer pipe
+    peak = lanes * ALG_PIPES[mode]
+    achieved = gcups * ALG_OPS_PER_CELL[mode]
+    maxima = gcups * ALU_MAX_OPS_PER_CELL[mode]
+    return {"bound": "alu", "achieved": round(achieved, 1), "peak": round(peak, 1), "unit": "Gop/s",
+            "frac": round(achieved / peak, 4), "ops_per_cell": ALG_OPS_PER_CELL[mode],
+            "pipes": ALG_PIPES[mode],
+            "frac_maxima_only": round(maxima / lanes, 4), "maxima_per_cell": ALU_MAX_OPS_PER_CELL[mode],
+            "peak_basis": f"{n_sm} SMs x {ALU_LANES_PER_SM_CLK} lanes/clk per integer pipe x "
+                          f"{ALG_PIPES[mode]} pipe(s) x {sm_mhz:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)",
+            "kernel_gcups": round(gcups, 1)}
 
 
 def parse():
@@ -58,8 +83,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the int32 and small-workload side measurements")
-    ap.add_argument("--serve-requests", type=int, default=600,
+    ap.add_argument("--serve-requests", type=int, default=10000,
                     help="requests of the serving run (Poisson 50/s, 500,000-protein database); 0 skips it")
+    ap.add_argument("--serve-half-requests", type=int, default=2500,
+                    help="requests of the second serving run at half the rate (25/s); 0 skips it")
     ap.add_argument("--mode", default="packed", choices=["packed", "int32"], help="form of the timed search")
     ap.add_argument("--no-query-pairs", action="store_true",
                     help="packed mode: keep every query in the two-sequences-per-chain form")
@@ -176,13 +203,16 @@ def measured_peaks():
         return {}
 
 
-def dp_kernel_traffic():
-    """DRAM bytes per launch of the DP kernel from the committed ncu summary,
-    or None if the kernel source changed since it was captured."""
+def dp_kernel_traffic(workload, mode="packed"):
+    """DRAM bytes per launch of the DP kernel on `workload` from the committed
+    ncu summary, or None if none was captured for that workload and form or
+    the kernel source changed since."""
     path = os.path.join(ROOT, "profiles", "dp_kernel_traffic.json")
     try:
         rec = json.load(open(path))
     except (OSError, ValueError):
+        return None
+    if rec.get("workload_name") != workload or rec.get("mode", "packed") != mode:
         return None
     if rec.get("source_sha1") != dp_kernel_source_sha1():
         return None
@@ -294,22 +324,132 @@ def time_prepared(pq, out, steps, flush, timing=False):
     return t_steps, k_steps
 
 
-def run_serving(n_requests, mode):
+def run_serving(n_requests, n_half, mode, gpu=0):
     """Continuous-batching serving runs on the serving_500k workload: 500,000 synthetic
     proteins (~180M residues) resident in HBM, queries (median 400, 30-3000)
     arriving as a Poisson process at 50/s (the first n_requests arrivals), and
-    the same arrival sequence at half the rate (25/s, the first n_requests / 2:
-    about half the sustained capacity).  Reports latency percentiles and
-    offered vs sustained GCUPS of each."""
+    the same arrival sequence at half the rate (25/s, the first n_half
+    arrivals: about half the sustained capacity).  Reports latency
+    percentiles, offered vs sustained GCUPS and the clocks of each run."""
     from paper_2412_08308_gb300 import api
     from workload import make_workload
 
-    w = make_workload("serving_500k", n_queries=n_requests)
+    w = make_workload("serving_500k", n_queries=max(n_requests, n_half))
     db = api.Database.from_sequences(w["db"])
+    clk = Clocks(gpu)
+    clk.start()
     st = serve_once(db, w, n_requests, 1.0, mode)
-    st["half_rate"] = serve_once(db, w, max(1, n_requests // 2), 2.0, mode)
+    st["clocks"] = clk.stop()
+    if n_half > 0:
+        clk = Clocks(gpu)
+        clk.start()
+        st["half_rate"] = serve_once(db, w, n_half, 2.0, mode)
+        st["half_rate"]["clocks"] = clk.stop()
     db.close()
     return st
+
+
+def graph_search_ms(pq, out, stream, flush, reps):
+    """Per-search times (ms) of sw_search_graph launches on `stream`, CUDA
+    events on that stream around each launch, L2 flushed before each."""
+    import torch
+
+    ts = []
+    for _ in range(reps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        stream.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pq.search_graph(out, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return ts
+
+
+def small_config_block(api, name, flush, gpu, n_sm, sm_mhz, reps=50):
+    """One of the small configurations (the 144-residue query against 2,000
+    proteins; the homolog workload) in both forms: whole searches replayed
+    through sw_search_graph (median of `reps`), the DP kernel's own time
+    (events around it in a plain enqueue), its ALU roofline, the pairs rescued
+    and the clocks sampled during the block."""
+    import torch
+
+    from workload import WORKLOADS, make_workload
+    from workload.matrices import BLOSUM62
+
+    w = make_workload(name)
+    q, dbs = w["queries"], w["db"]
+    cells = float(q.total) * float(dbs.total)
+    db = api.Database.from_sequences(dbs)
+    stream = torch.cuda.Stream()
+    out = torch.empty((len(q), len(dbs)), dtype=torch.int32, device="cuda")
+    clk = Clocks(gpu)
+    clk.start()
+    res = {"workload": f"{name}: {WORKLOADS[name]}", "cells": cells, "timed": "sw_search_graph, median of "
+           f"{reps} searches, L2 flushed before each"}
+    for mode in ("packed", "int32"):
+        pq = api.PreparedQueries(db, q.residues, q.offsets, BLOSUM62, 10, 2, mode, stream=stream)
+        for _ in range(3):
+            pq.search_graph(out, stream=stream)
+        rescued = pq.status(stream=stream)
+        ts = graph_search_ms(pq, out, stream, flush, reps)
+        pq.set_timing(True)
+        ks = []
+        for _ in range(min(reps, 20)):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            pq.search(out, stream=stream)
+            ks.append(pq.kernel_ms(stream=stream))
+        ms, kms = float(np.median(ts)), float(np.median(ks))
+        res[mode] = {"ms": round(ms, 4), "gcups": round(cells / ms / 1e6, 1), "dp_kernel_ms": round(kms, 4),
+                     "rescued_pairs": int(rescued), "launches_per_search": int(pq.info()[3]),
+                     "roofline": roofline_of(cells / kms / 1e6, mode, n_sm, sm_mhz)}
+        pq.close()
+    res["packed_over_int32"] = round(res["packed"]["gcups"] / res["int32"]["gcups"], 3)
+    res["clocks"] = clk.stop()
+    db.close()
+    return res
+
+
+def batch_config_block(api, flush, n_sm, sm_mhz):
+    """The 1,000-query batch against 50,000 proteins: the autotuner's sweep
+    (residues per thread x cutover) on the real batch, then both forms with
+    the tuned options, one graph-captured search each (median of 3)."""
+    import torch
+
+    from paper_2412_08308_gb300 import tune
+    from workload import WORKLOADS, make_workload
+    from workload.matrices import BLOSUM62
+
+    w = make_workload("thousand_queries_vs_50k")
+    q, dbs = w["queries"], w["db"]
+    cells = float(q.total) * float(dbs.total)
+    db = api.Database.from_sequences(dbs)
+    t0 = time.perf_counter()
+    opts, table = tune.tune(db, dbs.lengths, q.residues, q.offsets, BLOSUM62, rows=(4, 8, 16),
+                            cutovers=(512, 1024, 2048, 4096), reps=1)
+    tune_s = time.perf_counter() - t0
+    stream = torch.cuda.Stream()
+    out = torch.empty((len(q), len(dbs)), dtype=torch.int32, device="cuda")
+    res = {"workload": f"thousand_queries_vs_50k: {WORKLOADS['thousand_queries_vs_50k']}", "cells": cells,
+           "tuner": {"rows_per_lane": opts.rows_per_lane, "cutover": opts.cutover, "seconds": round(tune_s, 1),
+                     "table": [{"rows_per_lane": r, "cutover": c, "gcups": g} for r, c, g in table],
+                     "note": "database sequences are at most 1,000 residues, so cutovers 1024..4096 coincide"}}
+    for mode in ("packed", "int32"):
+        pq = api.PreparedQueries(db, q.residues, q.offsets, BLOSUM62, 10, 2, mode,
+                                 opts=opts if mode == "packed" else None, stream=stream)
+        pq.search_graph(out, stream=stream)
+        rescued = pq.status(stream=stream)
+        ts = graph_search_ms(pq, out, stream, flush, 3)
+        ms = float(np.median(ts))
+        res[mode] = {"ms": round(ms, 2), "gcups": round(cells / ms / 1e6, 1), "rescued_pairs": int(rescued),
+                     "roofline": roofline_of(cells / ms / 1e6, mode, n_sm, sm_mhz)}
+        pq.close()
+    res["packed_over_int32"] = round(res["packed"]["gcups"] / res["int32"]["gcups"], 3)
+    db.close()
+    return res
 
 
 def serve_once(db, w, n_requests, stretch, mode):
@@ -412,49 +552,34 @@ def run_ours(args, w):
     peaks = measured_peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count or SM_COUNT_FALLBACK
-    peak_gops = n_sm * ALU_LANES_PER_SM_CLK * sm_mhz * 1e6 / 1e9
-    achieved_gops = cells / k_mean / 1e9 * ALU_OPS_PER_CELL[args.mode]
-    roofline = {"bound": "alu", "achieved": round(achieved_gops, 1), "peak": round(peak_gops, 1),
-                "unit": "Gop/s", "frac": round(achieved_gops / peak_gops, 4), "traffic": dp_kernel_traffic(),
-                "kernel": ("inter_kernel, 16-bit forms (query pairs; two sequences per chain for unpaired queries)"
-                           if args.mode == "packed" else "inter_kernel, int32 form"),
-                "alu_ops_per_cell": ALU_OPS_PER_CELL[args.mode],
-                "peak_basis": f"{n_sm} SMs x {ALU_LANES_PER_SM_CLK} ALU-pipe lanes/clk x {sm_mhz:.0f} MHz "
-                              "(sm_max_mhz of MEASURED_PEAKS.json)",
-                "kernel_gcups": round(cells / k_mean / 1e9, 1)}
+    roofline = roofline_of(cells / k_mean / 1e9, args.mode, n_sm, sm_mhz)
+    roofline["traffic"] = dp_kernel_traffic(args.workload, args.mode) if not (args.queries or args.db_limit) else None
+    roofline["kernel"] = ("inter_kernel, 16-bit forms (query pairs; two sequences per chain for unpaired queries)"
+                          if args.mode == "packed" else "inter_kernel, int32 form")
 
     extras = {}
     if not args.no_extras and rank == 0:
+        xclk = Clocks(local)
+        xclk.start()
         # alignments of each query's best hits (sw_traceback)
         extras["traceback_top10"] = traceback_rate(api, db, q, out)
         # the plain int32 kernel (Algorithm 1 body) on the same workload
         pq32 = api.PreparedQueries(db, q.residues, q.offsets, BLOSUM62, 10, 2, "int32")
+        pq32.set_timing(True)
         pq32.search(out)
         torch.cuda.synchronize()
-        t32, _ = time_prepared(pq32, out, max(1, min(3, args.steps)), flush)
+        t32, k32 = time_prepared(pq32, out, max(1, min(3, args.steps)), flush, timing=True)
         extras["int32_gcups"] = round(cells * len(t32) / sum(t32) / 1e9, 1)
         extras["packed_over_int32"] = round(cells * args.steps / T / 1e9 / extras["int32_gcups"], 3)
+        extras["int32_roofline"] = roofline_of(cells / float(np.mean(k32)) / 1e9, "int32", n_sm, sm_mhz)
         pq32.close()
-        # the small single-query workload (1 query of 144 aa x 2,000 proteins)
-        from workload import make_workload
-
-        w1 = make_workload("one_query_vs_2k")
-        db1 = api.Database.from_sequences(w1["db"])
-        c1 = float(w1["queries"].total) * float(w1["db"].total)
-        out1 = torch.empty((1, len(w1["db"])), dtype=torch.int32, device="cuda")
-        g1 = {}
-        for mode in ("packed", "int32"):
-            p1 = api.PreparedQueries(db1, w1["queries"].residues, w1["queries"].offsets, BLOSUM62, 10, 2, mode)
-            for _ in range(3):
-                p1.search(out1)
-            ts, _ = time_prepared(p1, out1, 10, flush)
-            g1[mode] = c1 / float(np.median(ts)) / 1e9
-            p1.close()
-        db1.close()
-        extras["one_query_vs_2k"] = {"packed_gcups": round(g1["packed"], 1), "int32_gcups": round(g1["int32"], 1),
-                                           "ratio": round(g1["packed"] / g1["int32"], 3)}
+        # the other configurations of the method, each in both forms
+        extras["one_query_vs_2k"] = small_config_block(api, "one_query_vs_2k", flush, local, n_sm, sm_mhz)
+        extras["homologs_8k"] = small_config_block(api, "homologs_8k", flush, local, n_sm, sm_mhz, reps=10)
+        extras["thousand_queries_vs_50k"] = batch_config_block(api, flush, n_sm, sm_mhz)
         # the paper's DNA pairwise workload at its 1M x 1M size (sw_align_pair, int32)
         extras["dna_pair_1m_x_1m"] = dna_pair_gcups("dna_1m_x_1m")
+        extras["extras_clocks"] = xclk.stop()
 
     # end to end through sw_search with host buffers
     e2e = None
@@ -473,7 +598,7 @@ def run_ours(args, w):
 
     serving = None
     if rank == 0 and args.serve_requests > 0 and not (args.queries or args.db_limit):
-        serving = run_serving(args.serve_requests, args.mode)
+        serving = run_serving(args.serve_requests, args.serve_half_requests, args.mode, local)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -81,7 +81,13 @@ typedef struct sw_queries sw_queries;
 int sw_db_prepare(const uint8_t *residues, const int64_t *offsets, int64_t n_seqs,
                   void *stream, sw_db **out);
 
-/* Release a database and its device memory.  NULL is accepted. */
+/*
+ * sw_db_free -- release a database made by sw_db_prepare and its device
+ * memory (the protein database of the paper's search, Sec. 4.1, which stays
+ * resident between searches here).  NULL is accepted.  The caller must not free a database while a search that uses it
+ * may still run on a stream, nor while a prepared query batch planned against
+ * it is still in use.  Errors: none (always SW_OK).
+ */
 int sw_db_free(sw_db *db);
 
 /* Sizes of a prepared database: sequence count, residue count, device bytes. */
@@ -133,7 +139,14 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
 int sw_queries_free(sw_queries *q);
 
 /*
- * sw_search_prepared -- score every prepared query against the database.
+ * sw_search_prepared -- score every prepared query against the database:
+ * S(Q, D) = max over all cells of H of Eqs. 1-3 (Sec. 2.2) for every pair,
+ * with the batch's scoring (BLOSUM62 and gaps 10/2 in the paper's protein
+ * search, Sec. 4.1).  The int32 form runs the cell body of Algorithm 1; the
+ * packed form runs the same recurrences in 16-bit halves and recomputes in
+ * int32 every pair whose score could have left the 16-bit range (the paper's
+ * future work on lower-precision integers, Sec. 6), so both give the exact
+ * int32 score.
  *
  * Device-only and asynchronous: enqueues profile construction, the
  * dynamic-programming kernels, (packed mode) overflow detection and the exact
@@ -190,9 +203,21 @@ int sw_queries_info(const sw_queries *q, int64_t *h2d_bytes, int64_t *device_byt
                     int64_t *launches);
 
 /*
- * sw_search -- one-call search: prepare the queries, search, copy the scores
- * out, release the batch.  scores_out may be a host or a device pointer
- * (n_queries * n_db int32, caller order).  The call returns when the scores
+ * sw_search -- one-call database search: the local alignment score of Eqs.
+ * 1-3 (Sec. 2.2) for every (query, database sequence) pair, as the paper's
+ * protein database search computes it (Sec. 4.1: BLOSUM62, gaps 10/2, queries
+ * against a database of proteins).  Prepares the queries, searches, copies
+ * the scores out and releases the batch.
+ *
+ *   db                              a prepared database
+ *   queries, q_offsets, n_queries   host pointers, same layout as the database
+ *   submat, gap_open, gap_extend    see the conventions above
+ *   mode                            SW_MODE_INT32 or SW_MODE_PACKED (same scores)
+ *   scores_out  host or device pointer, n_queries * n_db int32, caller order;
+ *               owned by the caller
+ *   stream      stream for the work
+ *
+ * The call allocates and frees its own scratch and returns when the scores
  * are in place.  Errors: as sw_queries_prepare / sw_search_prepared, plus
  * SW_ETIMEOUT.
  */
@@ -208,11 +233,14 @@ int sw_search(const sw_db *db, const uint8_t *queries, const int64_t *q_offsets,
  * synchronise the device and stall every stream, a host that runs the library
  * inside an arena it does not control.)
  *
- * Every scratch buffer the search needs lives in one 16 MiB static device
- * array that each GPU loading this library holds until the process exits;
- * the call makes no cudaMalloc or cudaFree and calls no allocating library
- * routine.  It computes exact int32 scores with the inter-task kernel and
- * returns after they are in place (it synchronises `stream`).
+ * Every scratch buffer the search needs (the query profile, the task list,
+ * three counters) lives in one 16 MiB static device array that each GPU
+ * loading this library holds until the process exits; the call makes no
+ * cudaMalloc or cudaFree and calls no allocating library routine.  It
+ * computes exact int32 scores with the inter-task kernel, the whole query in
+ * one chunk of up to 32 lanes (16 rows per lane for queries of up to 512
+ * residues, 24 above), database sequences of every length included, and
+ * returns after the scores are in place (it synchronises `stream`).
  *
  *   db          a prepared database on the calling thread's current device
  *   query, m    host pointer to m residue codes 0..19, 0 <= m <= 768
@@ -220,8 +248,9 @@ int sw_search(const sw_db *db, const uint8_t *queries, const int64_t *q_offsets,
  *   scores_dev  DEVICE pointer to n_db int32, written in the caller's order
  *   stream      stream for the work (NULL = legacy default stream)
  *
- * Limits: queries of at most 768 residues, databases of at most 2,000,000
- * sequences; larger sizes are rejected with SW_EINVAL and a message.
+ * Limits: queries of at most 768 residues, databases of at most 8,000,000
+ * sequences, current devices 0..63; anything beyond is rejected with
+ * SW_EINVAL and a message.
  * The first call on a device looks up the device address of the scratch
  * array and configures the kernel; make that first call before any CUDA
  * stream capture on that device.  All calls on a device share the array and
@@ -329,7 +358,6 @@ int sw_traceback(const sw_db *db, const uint8_t *queries, const int64_t *q_offse
                  const sw_hit *hits, int64_t n_hits, const int8_t *submat, int32_t gap_open, int32_t gap_extend,
                  sw_alignment *out, uint8_t *ops, int64_t ops_capacity, void *stream);
 
-/* Message for the last failed call on this thread ("" if none). */
 /*
  * sw_selftest_wait -- check that the library's bounded device waits give up.
  * Every wait between warps or CTAs in the kernels (for a counter another warp
@@ -351,6 +379,14 @@ int sw_traceback(const sw_db *db, const uint8_t *queries, const int64_t *q_offse
  */
 int sw_selftest_wait(int32_t which, int64_t budget_cycles, int32_t *status_out, void *stream);
 
+/*
+ * sw_last_error -- the message of the last failed call on this thread, or ""
+ * if it succeeded.  The paper has no error interface; the message names the
+ * argument or CUDA call that failed (the status code of every entry point
+ * carries the class: SW_EINVAL, SW_ENOMEM, SW_ECUDA, SW_ETIMEOUT).  The
+ * string is owned by the library and stays valid until the next call of
+ * this library on the same thread.
+ */
 const char *sw_last_error(void);
 
 #ifdef __cplusplus

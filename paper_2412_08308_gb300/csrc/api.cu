@@ -189,6 +189,7 @@ void free_queries(sw_queries *q) {
 namespace swgb {
 const DbView &db_view(const sw_db *db) { return db->view; }
 int db_device(const sw_db *db) { return db->device; }
+const int32_t *db_ident(const sw_db *db) { return db->d_ident; }
 int64_t db_sorted_pos(const sw_db *db, int64_t caller_index) { return db->h_pos[caller_index]; }
 int32_t db_sorted_len(const sw_db *db, int64_t pos) { return db->h_len[pos]; }
 int32_t db_sorted_npad(const sw_db *db, int64_t pos) { return db->h_npad[pos]; }

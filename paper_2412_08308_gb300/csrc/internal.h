@@ -198,6 +198,8 @@ cudaError_t launch_rescue_tasks(const int32_t *flag_count, const QDesc *qd, int3
 // Accessors for translation units other than api.cu (the sw_db layout is private to it).
 const DbView &db_view(const struct ::sw_db *db);
 int db_device(const struct ::sw_db *db);
+// device [0, 1, ..., n - 1, n - 1]: sorted positions, usable as one-sequence units
+const int32_t *db_ident(const struct ::sw_db *db);
 int64_t db_sorted_pos(const struct ::sw_db *db, int64_t caller_index);  // caller order -> sorted position
 int32_t db_sorted_len(const struct ::sw_db *db, int64_t pos);           // true length at a sorted position
 int32_t db_sorted_npad(const struct ::sw_db *db, int64_t pos);          // padded length at a sorted position

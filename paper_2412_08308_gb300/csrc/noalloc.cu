@@ -5,8 +5,8 @@
 // real-time loop in which a cudaMalloc may synchronise the device and stall
 // every stream, or a host that runs this library inside a fixed arena it does
 // not control.  For them this entry point keeps every scratch buffer the
-// inter-task kernel needs (the query profile, the task list, the sequence
-// positions, the counters) in one file-scope __device__ array of
+// inter-task kernel needs (the query profile, the task list, the counters)
+// in one file-scope __device__ array of
 // kNoAllocScratchBytes.  Every GPU that loads the library holds that array
 // until the process exits; the caller passes the prepared database, the query
 // and the output buffer, and nothing is allocated per call.
@@ -21,7 +21,9 @@ namespace {
 
 constexpr size_t kNoAllocScratchBytes = 16u << 20;  // 16 MiB per device
 constexpr int kNoAllocMaxQuery = 768;               // one chunk: 32 lanes x 24 rows
-constexpr int64_t kNoAllocMaxSeqs = 2000000;
+// the task list takes 16 bytes per 8 sequences at most (chains of more than
+// 16 lanes: one chain per warp, 8 warps per CTA)
+constexpr int64_t kNoAllocMaxSeqs = 8000000;
 constexpr int kNoAllocThreads = 256;
 constexpr int kMaxDevices = 64;
 
@@ -34,7 +36,8 @@ constexpr size_t kOffSubmat = 512;   // 400 bytes
 constexpr size_t kOffQuery = 1024;   // up to kNoAllocMaxQuery residues
 constexpr size_t kOffProf = 2048;    // one profile chunk: 21 x round_up(L*R, 128) bytes
 constexpr size_t kProfMax = 21 * 768;
-constexpr size_t kOffPos = kOffProf + kProfMax;  // int32 positions, then the task list
+constexpr size_t kOffTasks = kOffProf + kProfMax;  // the task list
+static_assert(kOffTasks % 16 == 0, "tasks are 16-byte records");
 
 struct DeviceSetup {
   uint8_t *scratch = nullptr;  // device address of g_noalloc_scratch on this device
@@ -43,12 +46,12 @@ struct DeviceSetup {
 DeviceSetup g_setup[kMaxDevices];
 std::mutex g_setup_mutex;
 
-// Positions 0..n-1 (one database sequence per unit: the int32 form) and
-// tiles of `chains` consecutive units; the database is sorted longest first.
-__global__ void noalloc_plan_kernel(int32_t *pos, Task *tasks, int32_t n, int32_t chains, int32_t *n_tasks) {
+// Tiles of `chains` consecutive units (one database sequence per unit: the
+// int32 form, unit u = sorted position u); the database is sorted longest
+// first, so the tiles are too.
+__global__ void noalloc_plan_kernel(Task *tasks, int32_t n, int32_t chains, int32_t *n_tasks) {
   const int32_t nt = (n + chains - 1) / chains;
   const int32_t stride = gridDim.x * blockDim.x;
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) pos[i] = i;
   for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += stride) {
     Task tk;
     tk.q = 0;
@@ -108,9 +111,12 @@ extern "C" int sw_search_noalloc(const sw_db *db, const uint8_t *query, int64_t 
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_err(e, "cudaGetDevice");
-  if (dev != db_device(db) || dev >= kMaxDevices)
+  if (dev != db_device(db))
     return fail_msg(SW_EINVAL, "sw_search_noalloc: the current device %lld is not the database's device %lld", dev,
                     db_device(db));
+  if (dev >= kMaxDevices)
+    return fail_msg(SW_EINVAL, "sw_search_noalloc: device index %lld is beyond the %lld devices this entry point "
+                    "supports", dev, kMaxDevices);
   cudaPointerAttributes pa;
   if (cudaPointerGetAttributes(&pa, scores_dev) != cudaSuccess || pa.type != cudaMemoryTypeDevice) {
     cudaGetLastError();
@@ -152,14 +158,12 @@ extern "C" int sw_search_noalloc(const sw_db *db, const uint8_t *query, int64_t 
   const int warps = kNoAllocThreads / 32;
   const int chains = warps * (32 / L);
   const int64_t n_tasks = (n + chains - 1) / chains;
-  const size_t off_tasks = round_up(kOffPos + 4 * (size_t)n, 16);
-  if (off_tasks + sizeof(Task) * (size_t)n_tasks > kNoAllocScratchBytes)
+  if (kOffTasks + sizeof(Task) * (size_t)n_tasks > kNoAllocScratchBytes)
     return fail_msg(SW_EINVAL, "sw_search_noalloc: database of %lld sequences does not fit the scratch", (long long)n);
 
   uint8_t *scr = setup.scratch;
   int32_t *words = reinterpret_cast<int32_t *>(scr + kOffWords);
-  int32_t *pos = reinterpret_cast<int32_t *>(scr + kOffPos);
-  Task *tasks = reinterpret_cast<Task *>(scr + off_tasks);
+  Task *tasks = reinterpret_cast<Task *>(scr + kOffTasks);
   cudaStream_t s = (cudaStream_t)stream;
 
   // The scratch keeps the previous call's contents: counters start at zero.
@@ -170,9 +174,9 @@ extern "C" int sw_search_noalloc(const sw_db *db, const uint8_t *query, int64_t 
     return cuda_err(e, "upload");
   if (m > 0 && (e = cudaMemcpyAsync(scr + kOffQuery, query, (size_t)m, cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return cuda_err(e, "upload");
-  const int pgrid = (int)((n + kNoAllocThreads - 1) / kNoAllocThreads > 1024 ? 1024
-                                                                          : (n + kNoAllocThreads - 1) / kNoAllocThreads);
-  noalloc_plan_kernel<<<pgrid, kNoAllocThreads, 0, s>>>(pos, tasks, (int32_t)n, chains, words + 1);
+  const int64_t pblocks = (n_tasks + kNoAllocThreads - 1) / kNoAllocThreads;
+  const int pgrid = (int)(pblocks > 1024 ? 1024 : pblocks);
+  noalloc_plan_kernel<<<pgrid, kNoAllocThreads, 0, s>>>(tasks, (int32_t)n, chains, words + 1);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err(e, "plan kernel");
   Scoring sc{};
   sc.go = gap_open + gap_extend;
@@ -187,7 +191,7 @@ extern "C" int sw_search_noalloc(const sw_db *db, const uint8_t *query, int64_t 
 
   InterArgs a{};
   a.db = v;
-  a.unit_pos = pos;
+  a.unit_pos = db_ident(db);  // the database's own [0, 1, ..., n - 1]: unit u is sorted position u
   a.qd = reinterpret_cast<const QDesc *>(scr + kOffQDesc);
   a.tasks = tasks;
   a.n_tasks = words + 1;

@@ -255,15 +255,55 @@ def test_twenty_queries_vs_200k_sampled(api, mode):
     assert got.min() >= 0
 
 
-def test_thousand_queries_vs_50k_sampled(api):
-    # 1,000 queries against 50,000 sequences (packed); a sample of 12 queries
-    # x 150 sequences is checked
+@pytest.fixture(scope="module")
+def thousand():
     w = make_workload("thousand_queries_vs_50k")
-    got = _search(api, w["db"], w["queries"], "packed")
     qi = sample_indices(len(w["queries"]), 12, seed=4101)
     di = sample_indices(len(w["db"]), 150, seed=4102)
-    exp = oracle.scores(w["queries"].subset(qi), w["db"], BLOSUM62, 10, 2, subset=di)
+    w["sample"] = (qi, di, oracle.scores(w["queries"].subset(qi), w["db"], BLOSUM62, 10, 2, subset=di))
+    return w
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_thousand_queries_vs_50k_sampled(api, thousand, mode):
+    # 1,000 queries against 50,000 sequences in one batch, both forms; a
+    # sample of 12 queries x 150 sequences is checked against the oracle
+    w = thousand
+    got = _search(api, w["db"], w["queries"], mode)
+    qi, di, exp = w["sample"]
     _assert_equal(got[np.ix_(qi, di)], exp)
+    assert got.min() >= 0
+
+
+def serving_sample(w, k=16):
+    """About k seeded queries of the serving workload, its shortest and its
+    longest among them, and a seeded 300-sequence sample of its database."""
+    ql = w["queries"].lengths
+    qi = set(sample_indices(len(ql), k - 2, seed=4103).tolist()) | {int(np.argmin(ql)), int(np.argmax(ql))}
+    qi = np.array(sorted(qi), dtype=np.int64)
+    di = sample_indices(len(w["db"]), 300, seed=4104)
+    return qi, di
+
+
+@pytest.fixture(scope="module")
+def serving_500k():
+    w = make_workload("serving_500k")
+    qi, di = serving_sample(w)
+    q = w["queries"].subset(qi)
+    assert q.lengths.max() == w["queries"].lengths.max() and q.lengths.min() == w["queries"].lengths.min()
+    return w, q, di, oracle.scores(q, w["db"], BLOSUM62, 10, 2, subset=di)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_serving_500k_sampled(api, serving_500k, mode):
+    # the serving database at its full size (500,000 proteins, ~180M
+    # residues, resident) against 16 of its queries (30..3,000 residues,
+    # the longest included) in one batch; every score of a seeded
+    # 300-sequence sample is compared with the oracle
+    w, q, di, exp = serving_500k
+    got = _search(api, w["db"], q, mode)
+    _assert_equal(got[:, di], exp)
+    assert got.min() >= 0
 
 
 def test_prepared_repeat_and_device_output(api):
