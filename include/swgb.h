@@ -108,7 +108,14 @@ typedef struct sw_options {
                               into the two 16-bit halves where no lane can overflow (one
                               database sequence per chain), 1 = never pair (two database
                               sequences per chain for every query) */
-  int32_t reserved[3];     /* must be 0 */
+  int32_t band_stream;     /* batches too small to fill the GPU (0 = auto): queries of at least
+                              512 residues against every database unit, and the shorter queries
+                              against the units of at least `cutover` residues, run in the
+                              band-stream kernel -- a query's rows cut into bands of 256, one warp
+                              each, all bands of a query running as a pipeline over a stream of
+                              units (the intra-task kernel is not used); 1 = never; 2 = for every
+                              batch, however large */
+  int32_t reserved[2];     /* must be 0 */
 } sw_options;
 
 /*

@@ -128,6 +128,14 @@ struct sw_queries {
   uint2 *d_gbuf = nullptr, *d_igbuf = nullptr;
   int32_t *d_words = nullptr;
   int32_t *d_flag_pos = nullptr, *d_iflag_pos = nullptr;
+  // band-stream jobs (small batches): long queries against every unit, the
+  // other queries against the long units
+  int64_t n_bjobs = 0, n_bands = 0, n_btargets = 0, band_ring_bytes = 0;
+  int bgrid = 1;
+  BandJob *d_bjobs = nullptr;
+  int32_t *d_bjob_of = nullptr;
+  int2 *d_btpos = nullptr;
+  unsigned long long *d_brings = nullptr;
   int64_t h2d_bytes = 0;
   bool timing = false, timed = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -135,7 +143,7 @@ struct sw_queries {
   const sw_db *gdb = nullptr;
   int32_t *gscores = nullptr;
   // word layout: [0] inter counter, [1] inter rescue counter, [2] status, [3] inter rescue tasks,
-  // [4] intra (packed) counter, [5] intra (int32) counter, [6] query-pair counter, [7] unused,
+  // [4] intra (packed) counter, [5] intra (int32) counter, [6] query-pair counter, [7] band counter,
   // [8, 8+nq) inter flag counts, [8+nq, 8+2nq) intra flag counts   -- zeroed every search
   // [8+2nq] inter tasks, [9+2nq] intra packed tasks, [10+2nq] intra int32 tasks,
   // [11+2nq] query-pair tasks -- constants
@@ -314,8 +322,9 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
     return fail(SW_EINVAL, "sw_queries_prepare: gap penalties out of range (%d, %d)", gap_open, gap_extend);
   sw_options o{};
   if (opts) o = *opts;
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < 2; ++i)
     if (o.reserved[i]) return fail(SW_EINVAL, "sw_queries_prepare: reserved option fields must be 0");
+  if (o.band_stream < 0 || o.band_stream > 2) return fail(SW_EINVAL, "sw_queries_prepare: band_stream must be 0, 1 or 2");
   if (o.query_pairs != 0 && o.query_pairs != 1) return fail(SW_EINVAL, "sw_queries_prepare: query_pairs must be 0 or 1");
   int R = o.rows_per_lane ? o.rows_per_lane : 24;
   const int Ri = o.intra_rows ? o.intra_rows : 16;
@@ -426,6 +435,118 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   }
   const int threads = warps * 32;
   Q->threads = threads;
+  auto qlen = [&](int64_t q) { return (int32_t)(q_offsets[q + 1] - q_offsets[q]); };
+  auto may_flag = [&](int64_t q, int32_t n_upper) {
+    return packed && (int64_t)sc.maxp * std::min<int64_t>(qlen(q), n_upper) > sc.thresh;
+  };
+
+  // --- band-stream jobs (k_band.cu).  In a batch too small to fill the GPU,
+  // a query of at least two bands (512 rows) runs against every database
+  // unit, and a shorter query against the long units, as pipelines of
+  // 256-row bands, one warp each: a job is one query and a stream of units,
+  // all its bands sweeping the stream together.  A unit whose pair with the
+  // query could pass the 16-bit range is split into its sequences in int32;
+  // the others keep two sequences per 32-bit word.  Streams are cut so that
+  // every warp of one launch gets about the same number of columns (the
+  // longest unit at least), and their rings (one entry per stream column
+  // between consecutive bands) must fit a memory budget; otherwise the
+  // batch takes the regular plan.
+  std::vector<char> band_q(n_queries, 0);
+  std::vector<BandJob> bjobs;
+  std::vector<int32_t> bjob_of;
+  std::vector<int2> btpos;
+  bool band_mode = false;
+  if (o.band_stream != 1 && (o.band_stream == 2 || latency_bound) && n > 0 && n_queries > 0) {
+    const int brows = band_rows();
+    bool any = n_long > 0;
+    for (int64_t q = 0; q < n_queries; ++q) {
+      band_q[q] = qlen(q) >= 2 * brows;
+      any |= band_q[q] != 0;
+    }
+    const int bocc = any ? band_max_ctas_per_sm() : 0;
+    if (any && bocc > 0) {
+      struct BList {
+        int32_t q, packed, nb;
+        std::vector<int2> t;
+        std::vector<int32_t> w;  // columns of each unit
+        int64_t cols = 0;
+      };
+      std::vector<BList> lists;
+      double total = 0;
+      for (int64_t q = 0; q < n_queries; ++q) {
+        const int64_t u1 = band_q[q] ? Q->n_units : n_long;
+        if (u1 == 0) continue;
+        const int32_t nb = std::max(1, (qlen(q) + brows - 1) / brows);
+        BList lp{(int32_t)q, 1, nb, {}, {}, 0}, li{(int32_t)q, 0, nb, {}, {}, 0};
+        for (int64_t u = 0; u < u1; ++u) {
+          const int32_t a = unit_seq(packed ? 2 * u : u), b = packed ? unit_seq(2 * u + 1) : a;
+          if (packed && !may_flag(q, unit_len(u))) {
+            lp.t.push_back(make_int2(a, b));
+            lp.w.push_back(std::max(npad[a], npad[b]));
+            lp.cols += lp.w.back();
+          } else {
+            li.t.push_back(make_int2(a, a));
+            li.w.push_back(npad[a]);
+            li.cols += npad[a];
+            if (b != a) {
+              li.t.push_back(make_int2(b, b));
+              li.w.push_back(npad[b]);
+              li.cols += npad[b];
+            }
+          }
+        }
+        for (BList *L : {&lp, &li})
+          if (!L->t.empty()) {
+            total += (double)L->nb * (double)L->cols;
+            lists.push_back(std::move(*L));
+          }
+      }
+      const double wbudget = (double)sms * bocc * (band_threads() / 32);
+      const int64_t per_warp = std::max<int64_t>(1, (int64_t)std::ceil(total / wbudget));
+      for (const BList &L : lists) {
+        size_t i = 0;
+        while (i < L.t.size()) {
+          BandJob j{};
+          j.q = L.q;
+          j.packed = L.packed;
+          j.nb = L.nb;
+          j.t_begin = (int32_t)btpos.size();
+          int64_t cols = 0;
+          while (i < L.t.size() && (cols == 0 || cols + L.w[i] <= per_warp)) {
+            btpos.push_back(L.t[i]);
+            cols += L.w[i];
+            ++i;
+          }
+          j.t_count = (int32_t)(btpos.size() - j.t_begin);
+          j.cols = cols;
+          bjobs.push_back(j);
+        }
+      }
+      // longest streams first: their bands are handed out first
+      std::stable_sort(bjobs.begin(), bjobs.end(), [](const BandJob &x, const BandJob &y) {
+        return (int64_t)x.nb * x.cols > (int64_t)y.nb * y.cols;
+      });
+      int64_t ring = 0, band = 0;
+      for (size_t k = 0; k < bjobs.size(); ++k) {
+        bjobs[k].band0 = (int32_t)band;
+        bjobs[k].ring0 = ring;
+        ring += (int64_t)(bjobs[k].nb - 1) * bjobs[k].cols;
+        for (int b = 0; b < bjobs[k].nb; ++b) bjob_of.push_back((int32_t)k);
+        band += bjobs[k].nb;
+      }
+      const int64_t kBandRingBudget = (int64_t)4 << 30;
+      band_mode = 8 * ring <= kBandRingBudget && band < ((int64_t)1 << 30);
+      if (band_mode) {
+        Q->n_bjobs = (int64_t)bjobs.size();
+        Q->n_bands = band;
+        Q->n_btargets = (int64_t)btpos.size();
+        Q->band_ring_bytes = 8 * ring;
+        Q->bgrid = (int)std::max<int64_t>(1, std::min<int64_t>((band + band_threads() / 32 - 1) / (band_threads() / 32),
+                                                               (int64_t)sms * bocc));
+      }
+    }
+    if (!band_mode) std::fill(band_q.begin(), band_q.end(), 0);
+  }
 
   // --- query tracks (packed mode).  Two queries share one chain, one per
   // 16-bit half: the database residue of a column is common to both, so one
@@ -436,16 +557,12 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   // balanced tracks).  Only queries that cannot pass the 16-bit threshold
   // against the short database units join tracks (the form has no rescue
   // pass); the others keep the two-sequence form.
-  auto qlen = [&](int64_t q) { return (int32_t)(q_offsets[q + 1] - q_offsets[q]); };
-  auto may_flag = [&](int64_t q, int32_t n_upper) {
-    return packed && (int64_t)sc.maxp * std::min<int64_t>(qlen(q), n_upper) > sc.thresh;
-  };
   const int64_t s0 = packed ? std::min<int64_t>(n, 2 * n_long) : n_long;  // first short sequence
   Q->n_single = n - s0;
   std::vector<int32_t> in_track(n_queries, 0), elig;
   if (packed && o.query_pairs == 0 && n_queries >= 2 && Q->n_single > 0) {
     for (int64_t q = 0; q < n_queries; ++q)
-      if (!may_flag(q, max_short)) elig.push_back((int32_t)q);
+      if (!may_flag(q, max_short) && !band_q[q]) elig.push_back((int32_t)q);
     if (elig.size() < 2) elig.clear();
   }
   for (int32_t q : elig) in_track[q] = 1;
@@ -583,7 +700,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
     const int LR = d.L * R;
     d.nchunks = std::max(1, (d.m + LR - 1) / LR);
     d.chunk_stride = (int32_t)round_up((int64_t)profile_slots(d.L) * R, 128);
-    d.chunk_bytes = in_track[q] ? 0 : kProfRows * d.chunk_stride;
+    d.chunk_bytes = (in_track[q] || band_q[q]) ? 0 : kProfRows * d.chunk_stride;
     d.prof_off = prof;
     d.qoff = q_offsets[q];
     prof += (int64_t)d.nchunks * d.chunk_bytes;
@@ -637,7 +754,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
       chunked |= nc > 1;
     }
   }
-  if (n_long) {
+  if (n_long && !band_mode) {
     const int wmax = intra_threads() / 32;
     for (int64_t q = 0; q < n_queries; ++q) {
       QDesc &d = Q->qdi[q];
@@ -680,7 +797,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
     }
   }
   for (int64_t q = 0; q < n_queries && Q->n_units > n_long; ++q) {
-    if (in_track[q]) continue;
+    if (in_track[q] || band_q[q]) continue;
     const QDesc &d = Q->qd[q];
     const int chains = warps * (32 / d.L);
     for (int64_t u0 = n_long; u0 < Q->n_units; u0 += chains) {
@@ -693,7 +810,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   // long units: packed intra-task kernel where no lane can saturate, int32
   // otherwise (recomputing a saturated long matrix would cost more than
   // computing it once in int32)
-  for (int64_t q = 0; q < n_queries && n_long; ++q) {
+  for (int64_t q = 0; q < n_queries && n_long && !band_mode; ++q) {
     const QDesc &d = Q->qdi[q];
     for (int64_t u = 0; u < n_long; ++u) {
       const double w = (double)d.nchunks * d.L * d.R * (unit_len(u) + d.L);
@@ -782,8 +899,13 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   const size_t b_words = round_up(4 * (12 + 2 * nqm), 256);  // zeroed words + 3 constants
   const size_t b_flag = Q->inter_may_flag ? round_up(4 * nqm * std::max<int64_t>(n, 1), 256) : 0;
   const size_t b_iflag = packed ? round_up(4 * nqm * Q->long_stride, 256) : 0;
+  const size_t b_bjobs = round_up((int64_t)sizeof(BandJob) * std::max<int64_t>(Q->n_bjobs, 1), 256);
+  const size_t b_bjobof = round_up(4 * std::max<int64_t>(Q->n_bands, 1), 256);
+  const size_t b_btpos = round_up((int64_t)sizeof(int2) * std::max<int64_t>(Q->n_btargets, 1), 256);
+  const size_t b_brings = Q->n_bjobs ? round_up(std::max<int64_t>(Q->band_ring_bytes, 8), 256) : 0;
   Q->bytes = b_qres + b_sub + 2 * b_qd + b_tasks + b_itasks + b_itasks32 + b_ipos32 + b_rtasks + b_prof +
-             b_gbuf + b_igbuf + b_words + b_flag + b_iflag + b_qdp + b_ptasks + b_track;
+             b_gbuf + b_igbuf + b_words + b_flag + b_iflag + b_qdp + b_ptasks + b_track + b_bjobs + b_bjobof +
+             b_btpos + b_brings;
   cudaError_t e = cudaMallocAsync(&Q->block, Q->bytes, s);
   if (e != cudaSuccess) {
     delete Q;
@@ -813,6 +935,10 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   Q->d_qdp = (QDesc *)take(b_qdp);
   Q->d_track = (TrackChunk *)take(b_track);
   Q->d_ptasks = (Task *)take(b_ptasks);
+  Q->d_bjobs = (BandJob *)take(b_bjobs);
+  Q->d_bjob_of = (int32_t *)take(b_bjobof);
+  Q->d_btpos = (int2 *)take(b_btpos);
+  Q->d_brings = Q->n_bjobs ? (unsigned long long *)take(b_brings) : nullptr;
   Q->d_upos = const_cast<int32_t *>(db->d_ident) + s0;  // the short sequences, in sorted order
 
   std::vector<Task> tasks(Q->n_tasks), itasks(Q->n_itasks), itasks32(Q->n_itasks32), ptasks(Q->n_ptasks);
@@ -825,7 +951,8 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   Q->h2d_bytes = q_offsets[n_queries] + 400 + 2 * (int64_t)sizeof(QDesc) * n_queries +
                  (int64_t)sizeof(QDesc) * Q->npairs + (int64_t)sizeof(TrackChunk) * (int64_t)Q->track.size() +
                  (int64_t)sizeof(Task) * (Q->n_tasks + Q->n_itasks + Q->n_itasks32 + Q->n_ptasks) +
-                 4 * (int64_t)ipos32.size() + 16;
+                 4 * (int64_t)ipos32.size() + 16 + (int64_t)sizeof(BandJob) * Q->n_bjobs + 4 * Q->n_bands +
+                 (int64_t)sizeof(int2) * Q->n_btargets;
   e = cudaSuccess;
   if (q_offsets[n_queries] > 0)
     e = cudaMemcpyAsync(Q->d_qres, queries, q_offsets[n_queries], cudaMemcpyHostToDevice, s);
@@ -851,10 +978,17 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
     if (e == cudaSuccess && Q->n_ptasks)
       e = cudaMemcpyAsync(Q->d_ptasks, ptasks.data(), sizeof(Task) * Q->n_ptasks, cudaMemcpyHostToDevice, s);
   }
+  if (e == cudaSuccess && Q->n_bjobs) {
+    e = cudaMemcpyAsync(Q->d_bjobs, bjobs.data(), sizeof(BandJob) * Q->n_bjobs, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(Q->d_bjob_of, bjob_of.data(), 4 * Q->n_bands, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(Q->d_btpos, btpos.data(), sizeof(int2) * Q->n_btargets, cudaMemcpyHostToDevice, s);
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(Q->d_words, 0, b_words, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(Q->d_words + Q->zero_words(), consts, sizeof consts, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess && n_long) {
+  if (e == cudaSuccess && ((n_long && !band_mode) || Q->n_bjobs)) {
     e = cudaStreamCreateWithFlags(&Q->side, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&Q->fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&Q->join, cudaEventDisableTiming);
@@ -901,6 +1035,11 @@ int sw_search_prepared(const sw_db *db, const sw_queries *Q, int32_t *scores_dev
     SW_CUDA(launch_build_profiles(Q->d_qres, Q->d_qdi, nq, Q->d_submat, Q->sc.pad, Q->d_prof, s),
             "profile kernel");
 
+  // band-stream jobs add their scores with atomicMax: every score starts at 0
+  if (Q->n_bjobs) SW_CUDA(cudaMemsetAsync(scores_dev, 0, 4 * (size_t)Q->nq * (size_t)db->n, s), "memset");
+  const bool band_timing = Q->timing && Q->n_bjobs;
+  if (band_timing) SW_CUDA(cudaEventRecord(Q->ev0, s), "event");
+
   InterArgs a{};
   a.db = db->view;
   a.unit_pos = db->d_ident;
@@ -912,11 +1051,31 @@ int sw_search_prepared(const sw_db *db, const sw_queries *Q, int32_t *scores_dev
 
   // long database units: intra-task kernel on the side stream, concurrently;
   // int32 matrices (those that could saturate 16 bits) on a third stream
-  // when packed ones exist too, so that neither waits for the other
-  if (Q->n_long) {
+  // when packed ones exist too, so that neither waits for the other.  In
+  // small batches the band-stream jobs take the side stream instead.
+  if (Q->side) {
     SW_CUDA(cudaEventRecord(Q->fork, s), "event");
     SW_CUDA(cudaStreamWaitEvent(Q->side, Q->fork, 0), "event");
     if (Q->side2) SW_CUDA(cudaStreamWaitEvent(Q->side2, Q->fork, 0), "event");
+    if (Q->n_bjobs) {
+      SW_CUDA(cudaMemsetAsync(Q->d_brings, 0, (size_t)Q->band_ring_bytes, Q->side), "memset");
+      BandArgs ba{};
+      ba.db = db->view;
+      ba.tpos = Q->d_btpos;
+      ba.jobs = Q->d_bjobs;
+      ba.band_job = Q->d_bjob_of;
+      ba.nbands = (int32_t)Q->n_bands;
+      ba.band_counter = w + 7;
+      ba.qres = Q->d_qres;
+      ba.qd = Q->d_qd;
+      ba.submat = Q->d_submat;
+      ba.rings = Q->d_brings;
+      ba.out = scores_dev;
+      ba.out_stride = db->n;
+      ba.sc = Q->sc;
+      ba.status = w + 2;
+      SW_CUDA(launch_band(ba, Q->bgrid, Q->side), "band-stream kernel");
+    }
     InterArgs b = a;
     b.qd = Q->d_qdi;
     b.pbuf_bytes = Q->ipbuf_bytes;
@@ -947,7 +1106,7 @@ int sw_search_prepared(const sw_db *db, const sw_queries *Q, int32_t *scores_dev
     SW_CUDA(cudaEventRecord(Q->join, Q->side), "event");
   }
 
-  if (Q->timing && (Q->n_tasks || Q->n_ptasks)) SW_CUDA(cudaEventRecord(Q->ev0, s), "event");
+  if (Q->timing && !band_timing && (Q->n_tasks || Q->n_ptasks)) SW_CUDA(cudaEventRecord(Q->ev0, s), "event");
   if (Q->n_ptasks) {  // query pairs, one short database sequence per chain
     InterArgs p = a;
     p.qd = Q->d_qdp;
@@ -979,7 +1138,7 @@ int sw_search_prepared(const sw_db *db, const sw_queries *Q, int32_t *scores_dev
     a.flag_stride = db->n;
     SW_CUDA(launch_inter(a, Q->R, packed ? kFormPacked : kFormInt32, Q->grid, threads, Q->smem, s), "inter-task kernel");
   }
-  if (Q->timing && (Q->n_tasks || Q->n_ptasks)) {
+  if (Q->timing && !band_timing && (Q->n_tasks || Q->n_ptasks)) {
     SW_CUDA(cudaEventRecord(Q->ev1, s), "event");
     const_cast<sw_queries *>(Q)->timed = true;
   }
@@ -997,8 +1156,12 @@ int sw_search_prepared(const sw_db *db, const sw_queries *Q, int32_t *scores_dev
       SW_CUDA(launch_inter(r, Q->R, kFormInt32, Q->rgrid, threads, Q->smem, s), "inter-task rescue kernel");
     }
   }
-  if (Q->n_long) SW_CUDA(cudaStreamWaitEvent(s, Q->join, 0), "event");
+  if (Q->side) SW_CUDA(cudaStreamWaitEvent(s, Q->join, 0), "event");
   if (Q->side2) SW_CUDA(cudaStreamWaitEvent(s, Q->join2, 0), "event");
+  if (band_timing) {
+    SW_CUDA(cudaEventRecord(Q->ev1, s), "event");
+    const_cast<sw_queries *>(Q)->timed = true;
+  }
   return SW_OK;
 }
 
@@ -1089,6 +1252,7 @@ int sw_queries_info(const sw_queries *q, int64_t *h2d_bytes, int64_t *device_byt
       k += (q->n_tasks ? 1 : 0) + (q->n_ptasks ? 1 : 0);  // inter-task kernels
       k += (q->n_tasks && q->inter_may_flag) ? 2 : 0;     // rescue tasks + int32 rescue
       k += (q->n_itasks ? 1 : 0) + (q->n_itasks32 ? 1 : 0);
+      k += q->n_bjobs ? 1 : 0;  // band-stream kernel
     }
     *launches = k;
   }

@@ -129,6 +129,43 @@ size_t pair_smem_bytes(int pbuf_bytes, int warps);
 int pair_max_ctas_per_sm(int R, int threads, size_t smem);
 cudaError_t launch_pair(const PairBandArgs &a, int R, int grid, int threads, size_t smem, cudaStream_t s);
 
+// Band-stream kernel (k_band.cu): in small batches, a long query's rows (or a
+// short query's against long database units) cut into bands of 32 lanes x R
+// rows, one warp each, all bands of a job running as a pipeline over the
+// job's stream of database units.
+struct BandJob {
+  int32_t q;        // query: its rows are cut into the bands; its row of scores is written
+  int32_t packed;   // 1: a unit is two sequences in the 16-bit halves (pairs that cannot pass
+                    //    the 16-bit range); 0: one sequence, int32 cells
+  int32_t nb;       // bands (band_rows() query rows each)
+  int32_t t_begin;  // first unit in BandArgs::tpos
+  int32_t t_count;  // units of the stream, in order
+  int32_t band0;    // global index of the job's band 0
+  int64_t ring0;    // entry offset of the job's ring 0 (between bands 0 and 1) in BandArgs::rings
+  int64_t cols;     // columns of the stream (sum of the units' padded lengths): the length of each ring
+};
+struct BandArgs {
+  DbView db;
+  const int2 *tpos;           // units: sorted positions (A, B); B = A for one sequence
+  const BandJob *jobs;
+  const int32_t *band_job;    // [nbands] job of each global band (jobs' bands consecutive, in band order)
+  int32_t nbands;
+  int32_t *band_counter;      // device word, zeroed before the launch: hands out bands in index order
+  const uint8_t *qres;        // query residues
+  const QDesc *qd;            // m and qoff of every query
+  const int8_t *submat;       // 20x20
+  unsigned long long *rings;  // (nb - 1) rings of `cols` entries per job, zeroed before the launch
+  int32_t *out;               // [nq][out_stride] scores in caller order; the jobs' rows zeroed before
+  int64_t out_stride;
+  Scoring sc;
+  int32_t *status;            // SW_ETIMEOUT on an expired wait
+};
+int band_threads();
+int band_rows();
+size_t band_smem_bytes();
+int band_max_ctas_per_sm();  // plan time: raises the shared-memory limit; 0 on failure
+cudaError_t launch_band(const BandArgs &a, int grid, cudaStream_t s);
+
 // Traceback of selected hits (k_trace.cu): one warp per hit fills 4-bit
 // provenance codes per cell, one thread per hit walks them back.
 struct TraceHit {

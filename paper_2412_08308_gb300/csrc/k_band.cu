@@ -1,0 +1,327 @@
+// Band-stream kernel: long queries, and long database sequences, of small
+// batches (Sec. 2.2 Eqs. 1-3; Sec. 3.1 "long kernel"; Fig. 1 intra-sequence
+// parallelism), for sm_103a.
+//
+// In a small batch a long query (thousands of rows) against a few thousand
+// database sequences leaves the inter-task kernel one chain per database
+// unit, each chain sweeping its unit once per chunk of query rows, chunk
+// after chunk: the longest chains set the time while most SMs idle.  Here the
+// query's rows are cut into bands of 32 lanes x R rows, one warp each, and
+// all bands of a *job* -- a query and a stream of database units -- run as a
+// pipeline: the warp of band b sweeps the units of the stream one after the
+// other, and reads the bottom row of band b - 1 for each column from a ring
+// in global memory as soon as band b - 1 has written it.  A job's stream is
+// short enough (a few thousand columns) that many jobs run at once, and every
+// unit's cells are spread over all the job's warps instead of one.
+//
+// Forms: int32 cells (one database sequence per unit, Algorithm 1's
+// statements) or two sequences per unit in the 16-bit halves of a word (only
+// for pairs that cannot pass the 16-bit range, so no rescue is needed).  Both
+// use split lanes: a lane's upper R/2 rows work on column c, its lower R/2
+// rows on column c - 1.
+//
+// Rings and progress.  Each ring holds one 64-bit entry per column of the
+// job's whole stream, zeroed before the launch, and is written once: the
+// writer (band b's last lane) stores (H | 1 << 31, F) with one relaxed 64-bit
+// store, and the reader (band b + 1, lanes 0..15, a block of 16 columns ahead)
+// reloads until bit 31 is set.  H is below 2^31 (int32: bounded by the host;
+// 16-bit halves: both halves non-negative, so bit 31 is the high half's sign
+// bit, 0).  No band ever waits for a band below it (the rings never wrap), and
+// warps take their bands from an atomic counter in order, so every band a
+// warp waits on was taken earlier by a warp that is running: the pipeline
+// cannot deadlock whatever the launch's residency.  Every wait is bounded.
+//
+// Scores: each band keeps its running best per unit and adds it to the
+// caller-order output with atomicMax (the host zeroes the jobs' output rows
+// first); the maximum over the bands is the unit's score.
+#include "devutil.cuh"
+#include "dp_common.cuh"
+#include "internal.h"
+#include "../../include/swgb.h"
+
+namespace swgb {
+namespace {
+
+constexpr int kBandStreamThreads = 256;  // 8 warps, one band at a time each
+constexpr int kBR = 8;                   // rows per lane: bands of 256 query rows
+constexpr int kBandRows = 32 * kBR;
+constexpr int kLagS = 2 * 32 - 1;        // split lanes: the last lane trails the first by 63 columns
+constexpr int kProfBytes = kProfRows * kBandRows;              // a band's profile: [21][32 lanes x R] bytes
+constexpr int kWarpBytes = ((kProfBytes + 320) + 127) / 128 * 128;  // + residues 2 x 32 B, boundary 2 x 16 x 8 B
+constexpr int kSubmatBytes = 512;
+
+// A band's profile in the warp's shared-memory block: byte [c][lane * R + r]
+// = SM(Q[row], c) for row = band * 256 + lane * R + r, the pad value for the
+// pad residue (c = 20) and rows past the query's end.
+__device__ __forceinline__ void build_band_profile(uint8_t *prof, const int8_t *sm, const uint8_t *q, int m,
+                                                   int row0, int lane, int32_t pad) {
+  uint8_t codes[kBR];
+#pragma unroll
+  for (int r = 0; r < kBR; ++r) {
+    const int row = row0 + lane * kBR + r;
+    codes[r] = row < m ? q[row] : (uint8_t)kPadCode;
+  }
+  for (int c = 0; c < kProfRows; ++c) {
+#pragma unroll
+    for (int w = 0; w < kBR / 4; ++w) {
+      uint32_t v = 0;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int code = codes[4 * w + b];
+        const int32_t s = (c < kAlphabet && code < kAlphabet) ? (int32_t)sm[code * kAlphabet + c] : pad;
+        v |= ((uint32_t)s & 0xffu) << (8 * b);
+      }
+      *reinterpret_cast<uint32_t *>(prof + c * kBandRows + lane * kBR + 4 * w) = v;
+    }
+  }
+}
+
+// One band over one database unit (columns sbase .. sbase + npad - 1 of the
+// job's stream).  Returns false when a wait expired.
+template <int FORM>
+__device__ __forceinline__ bool band_unit(const BandArgs &a, const uint8_t *__restrict__ prof, uint8_t *ring,
+                                          const int lane, const int posA, const int posB, const int64_t sbase,
+                                          const unsigned long long *ring_in, unsigned long long *ring_out,
+                                          const Consts &cs, Word<FORM> &Sout) {
+  using W = Word<FORM>;
+  constexpr bool PACKED = FORM == kFormPacked;
+  constexpr int R = kBR;
+  const W H0 = (W)0;
+  const W F0 = PACKED ? (W)cs.F0W : (W)0;
+  const int npa = a.db.npad[posA];
+  const int npb = PACKED ? a.db.npad[posB] : 0;
+  const int npad = max(npa, npb);
+  const uint8_t *resA = a.db.res + a.db.off[posA];
+  const uint8_t *resB = a.db.res + a.db.off[posB];
+  const int nblk = (npad + kLagS + kColBlock - 1) / kColBlock;
+  const int nreal = npad / kColBlock;
+  const bool prev = ring_in != nullptr, next = ring_out != nullptr;
+  const bool lead = lane == 0;
+  const bool tail = lane == 31 && next;
+  const int src = lane > 0 ? lane - 1 : lane;
+
+  LaneState<R, FORM> st;
+  lane_reset(st, cs);
+  W outH = H0, outF = F0, S = (W)0;
+  uint32_t outRes = kPadPair, prevRes = kPadPair;
+  // split lanes: the lower half's diagonal H, incoming H (int32) and F, best
+  W hdiagB = H0, midH = H0, midF = F0, S2 = (W)0;
+  uint8_t *rres = ring;                              // [slot][2 seqs][16 B] residue codes
+  uint2 *rgb = reinterpret_cast<uint2 *>(ring + 64);  // [slot][16] (H, F) of the band above
+  const uint8_t *prow = prof + lane * R;
+  bool failed = false;
+
+  auto prefetch = [&](int blk) {
+    uint8_t *d = rres + (blk & 1) * 32;
+    const int col = blk * kColBlock;
+    if (col < npa) cp_async16(d, resA + col);
+    else *reinterpret_cast<uint4 *>(d) = make_uint4(0x14141414u, 0x14141414u, 0x14141414u, 0x14141414u);
+    if (PACKED) {
+      if (col < npb) cp_async16(d + 16, resB + col);
+      else *reinterpret_cast<uint4 *>(d + 16) = make_uint4(0x14141414u, 0x14141414u, 0x14141414u, 0x14141414u);
+    }
+    cp_async_commit();
+  };
+  if (lead) {
+    prefetch(0);
+    prefetch(1);
+  }
+
+  // reading side: the next block to load (lanes 0..15 hold one entry each)
+  int64_t rpos = sbase;
+  unsigned long long pend = 0ull;
+  auto load = [&]() {
+    if (lane < kColBlock) pend = ld_relaxed_u64(ring_in + rpos + lane);
+  };
+  // wait until the loaded entries are written, unpack them into `slot`, advance
+  auto land = [&](int slot) {
+    bool ok = lane >= kColBlock || (pend >> 31 & 1ull);
+    long long t0 = 0;
+    bool waited = false;
+    while (!__all_sync(0xffffffffu, ok)) {
+      if (!waited) {
+        t0 = clock64();
+        waited = true;
+      }
+      if (__any_sync(0xffffffffu, clock64() - t0 > kWaitBudgetCycles)) {
+        failed = true;
+        if (lead) atomicExch(a.status, SW_ETIMEOUT);
+        return;
+      }
+      if (!ok) {
+        __nanosleep(32);  // (a waiting band leaves the issue slots to the bands that compute)
+        pend = ld_relaxed_u64(ring_in + rpos + lane);
+        ok = (pend >> 31 & 1ull) != 0ull;
+      }
+    }
+    if (lane < kColBlock)
+      rgb[slot * kColBlock + lane] = make_uint2((uint32_t)pend & 0x7fffffffu, (uint32_t)(pend >> 32));
+    rpos += kColBlock;
+    __syncwarp();
+  };
+  // both boundary slots start as the matrix top boundary (a band without a
+  // band above keeps it; the others overwrite them block by block)
+  if (lane < kColBlock) {
+    rgb[lane] = make_uint2((uint32_t)H0, (uint32_t)F0);
+    rgb[kColBlock + lane] = make_uint2((uint32_t)H0, (uint32_t)F0);
+  }
+  __syncwarp();
+  if (prev && nreal > 0) {
+    load();
+    land(0);
+    if (!failed && nreal > 1) load();
+  }
+
+  int64_t wpos = sbase;
+  for (int blk = 0; blk < nblk && !failed; ++blk) {
+    const uint2 *gslot = rgb + (blk & 1) * kColBlock;
+    const uint32_t *rw = reinterpret_cast<const uint32_t *>(rres + (blk & 1) * 32);
+    if (lead) cp_async_wait<1>();
+#pragma unroll 1
+    for (int g4 = 0; g4 < kColBlock / 4; ++g4) {
+      const uint32_t wa = rw[g4], wb = PACKED ? rw[4 + g4] : 0u;  // (used by lane 0 only)
+#pragma unroll
+      for (int s4 = 0; s4 < 4; ++s4) {
+        const int s = g4 * 4 + s4;
+        const int t = blk * kColBlock + s;
+        W inH = (W)__shfl_sync(0xffffffffu, outH, src);
+        W inF = (W)__shfl_sync(0xffffffffu, outF, src);
+        uint32_t inRes = __shfl_sync(0xffffffffu, outRes, src);
+        if (lead) {
+          // (the residue ring holds the pad code past the unit's end, the
+          // boundary slot the top boundary where no band lies above)
+          inRes = PACKED ? prmt(wa, wb, sel_pair(s4)) : prmt(wa, 0u, sel_one(s4));
+          const uint2 v = gslot[s];
+          inH = (W)v.x;
+          inF = (W)v.y;
+        }
+        if constexpr (PACKED) {
+          uint32_t s1 = (uint32_t)S, s2 = (uint32_t)S2, hb = (uint32_t)hdiagB, mf = (uint32_t)midF, oh, of;
+          column_step_split<R, FORM>(st, hb, mf, prow, kBandRows, inRes, prevRes, (uint32_t)inH, (uint32_t)inF, cs,
+                                     s1, s2, oh, of, 0);
+          S = (W)s1;
+          S2 = (W)s2;
+          hdiagB = (W)hb;
+          midF = (W)mf;
+          outH = (W)oh;
+          outF = (W)of;
+        } else {
+          int32_t s1 = (int32_t)S, s2 = (int32_t)S2, hb = (int32_t)hdiagB, mh = (int32_t)midH, mf = (int32_t)midF;
+          int32_t oh, of;
+          column_step_split_int<R>(st, hb, mh, mf, prow, kBandRows, inRes, prevRes, (int32_t)inH, (int32_t)inF, cs,
+                                   s1, s2, oh, of);
+          S = (W)s1;
+          S2 = (W)s2;
+          hdiagB = (W)hb;
+          midH = (W)mh;
+          midF = (W)mf;
+          outH = (W)oh;
+          outF = (W)of;
+        }
+        outRes = prevRes;
+        prevRes = inRes;
+        if (tail) {
+          const int j = t - kLagS;
+          if (j >= 0 && j < npad) {
+            const uint32_t lo = (uint32_t)outH | 0x80000000u;
+            st_relaxed_u64(ring_out + wpos, ((unsigned long long)(uint32_t)outF << 32) | lo);
+            ++wpos;
+          }
+        }
+      }
+    }
+    if (lead) {
+      if (blk + 2 < nblk) prefetch(blk + 2);
+      else cp_async_commit();
+    }
+    if (prev && blk + 1 < nreal) {
+      land((blk + 1) & 1);
+      if (!failed && blk + 2 < nreal) load();
+    } else if (prev && blk + 1 < nblk) {
+      // the padding blocks after the last real one: top boundary again
+      if (lane < kColBlock) rgb[((blk + 1) & 1) * kColBlock + lane] = make_uint2((uint32_t)H0, (uint32_t)F0);
+      __syncwarp();
+    }
+  }
+  if (lead) cp_async_wait<0>();
+  Sout = score_max<FORM>(S, S2);
+  return !failed;
+}
+
+__global__ void __launch_bounds__(kBandStreamThreads, 2) band_stream_kernel(const BandArgs a) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  int8_t *sm = reinterpret_cast<int8_t *>(smem);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint8_t *prof = smem + kSubmatBytes + (size_t)warp * kWarpBytes;
+  uint8_t *ring = prof + kProfBytes;
+  for (int i = threadIdx.x; i < kAlphabet * kAlphabet; i += blockDim.x) sm[i] = a.submat[i];
+  __syncthreads();
+  const Consts cs = make_consts(a.sc);
+
+  for (;;) {
+    int g = 0;
+    if (lane == 0) g = atomicAdd(a.band_counter, 1);
+    g = __shfl_sync(0xffffffffu, g, 0);
+    if (g >= a.nbands) break;
+    const BandJob job = a.jobs[a.band_job[g]];
+    const int b = g - job.band0;
+    const QDesc qd = a.qd[job.q];
+    __syncwarp();
+    build_band_profile(prof, sm, a.qres + qd.qoff, qd.m, b * kBandRows, lane, a.sc.pad);
+    __syncwarp();
+    const unsigned long long *ring_in = b > 0 ? a.rings + job.ring0 + (int64_t)(b - 1) * job.cols : nullptr;
+    unsigned long long *ring_out = b + 1 < job.nb ? a.rings + job.ring0 + (int64_t)b * job.cols : nullptr;
+    int32_t *orow = a.out + (int64_t)job.q * a.out_stride;
+    int64_t sbase = 0;
+    bool ok = true;
+    for (int t = 0; t < job.t_count && ok; ++t) {
+      const int2 p = a.tpos[job.t_begin + t];
+      if (job.packed) {
+        uint32_t S = 0u;
+        ok = band_unit<kFormPacked>(a, prof, ring, lane, p.x, p.y, sbase, ring_in, ring_out, cs, S);
+        for (int d = 16; d > 0; d >>= 1) S = __vmaxs2(S, __shfl_xor_sync(0xffffffffu, S, d));
+        if (ok && lane == 0) {
+          atomicMax(&orow[a.db.perm[p.x]], (int32_t)(S & 0xffffu));
+          if (p.y != p.x) atomicMax(&orow[a.db.perm[p.y]], (int32_t)(S >> 16));
+        }
+        sbase += max(a.db.npad[p.x], a.db.npad[p.y]);
+      } else {
+        int32_t S = 0;
+        ok = band_unit<kFormInt32>(a, prof, ring, lane, p.x, p.x, sbase, ring_in, ring_out, cs, S);
+        for (int d = 16; d > 0; d >>= 1) S = max(S, __shfl_xor_sync(0xffffffffu, S, d));
+        if (ok && lane == 0) atomicMax(&orow[a.db.perm[p.x]], S);
+        sbase += a.db.npad[p.x];
+      }
+    }
+    __syncwarp();
+    if (!ok) break;
+  }
+}
+
+}  // namespace
+
+int band_threads() { return kBandStreamThreads; }
+int band_rows() { return kBandRows; }
+size_t band_smem_bytes() { return kSubmatBytes + (size_t)(kBandStreamThreads / 32) * kWarpBytes; }
+
+int band_max_ctas_per_sm() {
+  if (cudaFuncSetAttribute(band_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)band_smem_bytes()) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, band_stream_kernel, kBandStreamThreads, band_smem_bytes()) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+cudaError_t launch_band(const BandArgs &a, int grid, cudaStream_t s) {
+  band_stream_kernel<<<grid, kBandStreamThreads, band_smem_bytes(), s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace swgb

@@ -76,7 +76,7 @@ def test_ragged_tiles(api, mode, R, L):
     # database lengths straddling every padding boundary, empty and 1-residue
     # sequences, queries from 0 residues to several chunks of L*R rows
     db, q = _ragged(10 + R + L, 301, 9, 900)
-    got = _search(api, db, q, mode, opts=api.options(rows_per_lane=R, lanes_per_chain=L))
+    got = _search(api, db, q, mode, opts=api.options(rows_per_lane=R, lanes_per_chain=L, band_stream="never"))
     _assert_equal(got, oracle.scores(q, db, BLOSUM62, 10, 2))
 
 
@@ -121,8 +121,9 @@ def test_wider_matrices_and_gap_schemes(api, scale, go, ge):
         assert exp.max() > 32767
     for mode in MODES:
         for cutover in (1000, 4096):
-            got = _search(api, db, q, mode, sm=sm, go=go, ge=ge, opts=api.options(cutover=cutover))
-            _assert_equal(got, exp)
+            for band in ("never", "always"):
+                got = _search(api, db, q, mode, sm=sm, go=go, ge=ge, opts=api.options(cutover=cutover, band_stream=band))
+                _assert_equal(got, exp)
 
 
 def test_packed_overflow_is_rescued_exactly(api):
@@ -140,12 +141,16 @@ def test_packed_overflow_is_rescued_exactly(api):
     q = from_list([base, base[:100], rng.integers(0, 20, size=300).astype(np.uint8)])
     exp = oracle.scores(q, db, sm, 10, 2)
     assert exp.max() > 32767
-    pq = api.PreparedQueries(api.Database.from_sequences(db), q.residues, q.offsets, sm, 10, 2, "packed")
+    pq = api.PreparedQueries(api.Database.from_sequences(db), q.residues, q.offsets, sm, 10, 2, "packed",
+                             opts=api.options(band_stream="never"))
     got = pq.search().cpu().numpy()
     rescued = pq.status()
     _assert_equal(got, exp)
     assert rescued >= 4
     pq.close()
+    # the same batch with the 700-residue query on band-stream jobs: its
+    # saturating pairs run in int32 there, exact without a rescue
+    _assert_equal(_search(api, db, q, "packed", sm=sm, opts=api.options(band_stream="always")), exp)
 
 
 def _prepared(api, db_seqs, q_seqs, mode, sm=BLOSUM62, go=10, ge=2, opts=None):
@@ -172,8 +177,8 @@ def test_query_pairs(api, cutover):
     ql = [300, 290, 281, 250, 700, 100, 96, 55, 0, 0, 17, 16]
     q = from_list([rng.integers(0, 20, size=L).astype(np.uint8) for L in ql])
     exp = oracle.scores(q, db, BLOSUM62, 10, 2)
-    on, _ = _prepared(api, db, q, "packed", opts=api.options(cutover=cutover))
-    off, _ = _prepared(api, db, q, "packed", opts=api.options(cutover=cutover, query_pairs=False))
+    on, _ = _prepared(api, db, q, "packed", opts=api.options(cutover=cutover, band_stream="never"))
+    off, _ = _prepared(api, db, q, "packed", opts=api.options(cutover=cutover, query_pairs=False, band_stream="never"))
     _assert_equal(on, exp)
     _assert_equal(off, exp)
 
@@ -193,10 +198,11 @@ def test_query_pairs_only_where_no_lane_can_overflow(api):
     q = from_list([base, base[::-1].copy(), base[:40].copy(), rng.integers(0, 20, size=38).astype(np.uint8)])
     exp = oracle.scores(q, db, sm, 10, 2)
     assert exp.max() > 32767
-    got, info = _prepared(api, db, q, "packed", sm=sm, opts=api.options(cutover=4096))
+    got, info = _prepared(api, db, q, "packed", sm=sm, opts=api.options(cutover=4096, band_stream="never"))
     _assert_equal(got, exp)
     # the track plan adds its profile build and its inter-task launch
-    _, info_off = _prepared(api, db, q, "packed", sm=sm, opts=api.options(cutover=4096, query_pairs=False))
+    _, info_off = _prepared(api, db, q, "packed", sm=sm,
+                            opts=api.options(cutover=4096, query_pairs=False, band_stream="never"))
     assert info[3] == info_off[3] + 2
 
 
@@ -210,7 +216,7 @@ def test_query_pairs_tiles(api, R, L):
     db, _ = _ragged(40 + R + L, 257, 3, 10)
     rng = np.random.Generator(np.random.PCG64(R + L))
     q = from_list([rng.integers(0, 20, size=n).astype(np.uint8) for n in (900, 880, 333, 300, 5, 4, 17, 16, 1)])
-    got = _search(api, db, q, "packed", opts=api.options(rows_per_lane=R, lanes_per_chain=L))
+    got = _search(api, db, q, "packed", opts=api.options(rows_per_lane=R, lanes_per_chain=L, band_stream="never"))
     _assert_equal(got, oracle.scores(q, db, BLOSUM62, 10, 2))
 
 
@@ -222,22 +228,28 @@ def homologs():
     return w
 
 
-@pytest.mark.parametrize("mode,cutover", [("int32", 0), ("packed", 0), ("packed", 16384)])
-def test_homologs_precision_path(api, homologs, mode, cutover):
+@pytest.mark.parametrize("mode,cutover,band", [("int32", 0, "never"), ("packed", 0, "never"),
+                                               ("packed", 16384, "never"), ("int32", 0, "auto"),
+                                               ("packed", 0, "auto"), ("packed", 16384, "auto")])
+def test_homologs_precision_path(api, homologs, mode, cutover, band):
     # the 2,000-protein database plus 10 planted ~8,000-residue homologs of an
-    # 8,000-residue query, whose scores exceed the 16-bit range.  With the
-    # default cutover the homologs run in the intra-task kernel, which takes
-    # them straight to int32 (their bound max(SM)*min(m, n) passes the 16-bit
-    # threshold); with cutover 16384 they run packed in the inter-task kernel,
-    # saturate, are flagged and rescued exactly.
+    # 8,000-residue query, whose scores exceed the 16-bit range.  Without
+    # band-stream jobs: with the default cutover the homologs run in the
+    # intra-task kernel, which takes them straight to int32 (their bound
+    # max(SM)*min(m, n) passes the 16-bit threshold); with cutover 16384 they
+    # run packed in the inter-task kernel, saturate, are flagged and rescued
+    # exactly.  With them (the default for this small batch): the
+    # 8,000-residue query runs in 32 bands against every unit, the homologs in
+    # int32, the others packed; the 144-residue query against the homologs in
+    # one band.
     w = homologs
     db = api.Database.from_sequences(w["db"])
     pq = api.PreparedQueries(db, w["queries"].residues, w["queries"].offsets, BLOSUM62, 10, 2, mode,
-                             opts=api.options(cutover=cutover))
+                             opts=api.options(cutover=cutover, band_stream=band))
     got = pq.search().cpu().numpy()
     rescued = pq.status()
     _assert_equal(got, w["expected"])
-    if mode == "packed" and cutover == 16384:
+    if mode == "packed" and cutover == 16384 and band == "never":
         assert rescued >= len(w["homolog_ids"])
     pq.close()
     db.close()
@@ -372,7 +384,7 @@ def test_intra_task_kernel(api, mode, intra_rows):
     db = from_list([rng.integers(0, 20, size=int(L)).astype(np.uint8) for L in lens])
     ql = [0, 1, 33, 511, 512, 513, 3000, 4097, 9000]
     q = from_list([rng.integers(0, 20, size=int(L)).astype(np.uint8) for L in ql])
-    got = _search(api, db, q, mode, opts=api.options(cutover=1000, intra_rows=intra_rows))
+    got = _search(api, db, q, mode, opts=api.options(cutover=1000, intra_rows=intra_rows, band_stream="never"))
     _assert_equal(got, oracle.scores(q, db, BLOSUM62, 10, 2))
 
 
@@ -380,7 +392,7 @@ def test_intra_task_kernel(api, mode, intra_rows):
 def test_everything_intra(api, mode):
     # cutover 1: every unit goes through the intra-task kernel
     db, q = _ragged(91, 60, 5, 700)
-    got = _search(api, db, q, mode, opts=api.options(cutover=1))
+    got = _search(api, db, q, mode, opts=api.options(cutover=1, band_stream="never"))
     _assert_equal(got, oracle.scores(q, db, BLOSUM62, 10, 2))
 
 
@@ -399,7 +411,8 @@ def test_intra_saturating_units_exact(api):
     exp = oracle.scores(q, db, sm, 10, 2)
     assert exp.max() > 32767
     dbh = api.Database.from_sequences(db)
-    pq = api.PreparedQueries(dbh, q.residues, q.offsets, sm, 10, 2, "packed", opts=api.options(cutover=1000))
+    pq = api.PreparedQueries(dbh, q.residues, q.offsets, sm, 10, 2, "packed",
+                             opts=api.options(cutover=1000, band_stream="never"))
     got = pq.search().cpu().numpy()
     rescued = pq.status()
     _assert_equal(got, exp)
@@ -414,7 +427,9 @@ def test_bad_options_rejected(api):
     db_s = random_sequences(37, 10, 50, 0.5, 1, 100)
     q = random_sequences(38, 2, 50, 0.5, 1, 100)
     db = api.Database.from_sequences(db_s)
-    for opts in (api.options(rows_per_lane=7), api.options(lanes_per_chain=3), api.options(intra_rows=12)):
+    bad_band = api.options()
+    bad_band.band_stream = 3
+    for opts in (api.options(rows_per_lane=7), api.options(lanes_per_chain=3), api.options(intra_rows=12), bad_band):
         with pytest.raises(SwError) as e:
             api.PreparedQueries(db, q.residues, q.offsets, BLOSUM62, 10, 2, "packed", opts=opts)
         assert e.value.code == SW_EINVAL
@@ -469,3 +484,46 @@ def test_autotuner_picks_a_correct_plan(api, tmp_path):
     got = _search(api, db_s, q_s, "packed", opts=opts)
     _assert_equal(got, oracle.scores(q_s, db_s, BLOSUM62, 10, 2))
     db.close()
+
+
+def _band_db(seed, n, long_lens):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    edge = [0, 1, 2, 15, 16, 17, 47, 48, 49, 127, 128, 129]
+    lens = edge + list(long_lens) + list(rng.integers(1, 700, size=n - len(edge) - len(long_lens)))
+    rng.shuffle(lens)
+    return from_list([rng.integers(0, 20, size=int(L)).astype(np.uint8) for L in lens])
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("band", ["auto", "always"])
+def test_band_stream_ragged(api, mode, band):
+    # band-stream jobs (k_band.cu): queries across the band edges (256 rows a
+    # band: 511/512/513, 768/769 rows) and up to 12 bands, against a database
+    # with every padding edge and sequences at and past the cutover of 2,048
+    # residues (the queries below 512 rows meet those long units in one band
+    # each; the others every unit in their own band pipelines)
+    db = _band_db(511, 260, [2047, 2048, 2049, 3001, 5000])
+    rng = np.random.Generator(np.random.PCG64(512))
+    ql = [0, 1, 144, 255, 256, 257, 511, 512, 513, 768, 769, 1500, 3000]
+    q = from_list([rng.integers(0, 20, size=L).astype(np.uint8) for L in ql])
+    got = _search(api, db, q, mode, opts=api.options(band_stream=band))
+    _assert_equal(got, oracle.scores(q, db, BLOSUM62, 10, 2))
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_band_stream_saturating_and_asymmetric(api, mode):
+    # an asymmetric matrix with +60 matches: the band pipelines' pairs that
+    # can pass 32767 (a 3,000-residue query against copies of 700 to 2,400 of
+    # its residues) run in int32, the others two sequences per word; all exact
+    rng = np.random.Generator(np.random.PCG64(513))
+    sm = rng.integers(-20, 6, size=(20, 20)).astype(np.int8)
+    np.fill_diagonal(sm, 60)
+    base = rng.integers(0, 20, size=3000).astype(np.uint8)
+    seqs = [rng.integers(0, 20, size=int(rng.integers(10, 900))).astype(np.uint8) for _ in range(180)]
+    seqs[4], seqs[50], seqs[51], seqs[120] = base[:700].copy(), base[200:2600].copy(), base[:1500].copy(), base[::2]
+    db = from_list(seqs)
+    q = from_list([base, base[:600].copy(), base[2000:].copy(), rng.integers(0, 20, size=90).astype(np.uint8)])
+    exp = oracle.scores(q, db, sm, 9, 3)
+    assert exp.max() > 32767
+    got = _search(api, db, q, mode, sm=sm, go=9, ge=3, opts=api.options(band_stream="always", cutover=1000))
+    _assert_equal(got, exp)
