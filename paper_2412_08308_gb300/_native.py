@@ -44,7 +44,7 @@ class SwOptions(ctypes.Structure):
 
     _fields_ = [("cutover", ctypes.c_int32), ("rows_per_lane", ctypes.c_int32), ("lanes_per_chain", ctypes.c_int32),
                 ("intra_rows", ctypes.c_int32), ("query_pairs", ctypes.c_int32), ("band_stream", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("band_rows", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class SwError(RuntimeError):

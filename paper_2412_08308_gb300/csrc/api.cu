@@ -41,6 +41,7 @@ int cuda_fail(cudaError_t e, const char *what) {
 
 inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
+
 int sm_count(int dev) {
   int n = 0;
   cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
@@ -131,7 +132,7 @@ struct sw_queries {
   // band-stream jobs (small batches): long queries against every unit, the
   // other queries against the long units
   int64_t n_bjobs = 0, n_bands = 0, n_btargets = 0, band_ring_bytes = 0;
-  int bgrid = 1;
+  int bgrid = 1, bR = 8;
   BandJob *d_bjobs = nullptr;
   int32_t *d_bjob_of = nullptr;
   int2 *d_btpos = nullptr;
@@ -322,8 +323,9 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
     return fail(SW_EINVAL, "sw_queries_prepare: gap penalties out of range (%d, %d)", gap_open, gap_extend);
   sw_options o{};
   if (opts) o = *opts;
-  for (int i = 0; i < 2; ++i)
-    if (o.reserved[i]) return fail(SW_EINVAL, "sw_queries_prepare: reserved option fields must be 0");
+  if (o.reserved[0]) return fail(SW_EINVAL, "sw_queries_prepare: reserved option fields must be 0");
+  const int bR = o.band_rows ? o.band_rows : 8;
+  if (!band_supported_R(bR)) return fail(SW_EINVAL, "sw_queries_prepare: band_rows must be 8 or 16");
   if (o.band_stream < 0 || o.band_stream > 2) return fail(SW_EINVAL, "sw_queries_prepare: band_stream must be 0, 1 or 2");
   if (o.query_pairs != 0 && o.query_pairs != 1) return fail(SW_EINVAL, "sw_queries_prepare: query_pairs must be 0 or 1");
   int R = o.rows_per_lane ? o.rows_per_lane : 24;
@@ -457,13 +459,13 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   std::vector<int2> btpos;
   bool band_mode = false;
   if (o.band_stream != 1 && (o.band_stream == 2 || latency_bound) && n > 0 && n_queries > 0) {
-    const int brows = band_rows();
+    const int brows = 32 * bR;
     bool any = n_long > 0;
     for (int64_t q = 0; q < n_queries; ++q) {
       band_q[q] = qlen(q) >= 2 * brows;
       any |= band_q[q] != 0;
     }
-    const int bocc = any ? band_max_ctas_per_sm() : 0;
+    const int bocc = any ? band_max_ctas_per_sm(bR) : 0;
     if (any && bocc > 0) {
       struct BList {
         int32_t q, packed, nb;
@@ -541,6 +543,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
         Q->n_bands = band;
         Q->n_btargets = (int64_t)btpos.size();
         Q->band_ring_bytes = 8 * ring;
+        Q->bR = bR;
         Q->bgrid = (int)std::max<int64_t>(1, std::min<int64_t>((band + band_threads() / 32 - 1) / (band_threads() / 32),
                                                                (int64_t)sms * bocc));
       }
@@ -1074,7 +1077,7 @@ int sw_search_prepared(const sw_db *db, const sw_queries *Q, int32_t *scores_dev
       ba.out_stride = db->n;
       ba.sc = Q->sc;
       ba.status = w + 2;
-      SW_CUDA(launch_band(ba, Q->bgrid, Q->side), "band-stream kernel");
+      SW_CUDA(launch_band(ba, Q->bR, Q->bgrid, Q->side), "band-stream kernel");
     }
     InterArgs b = a;
     b.qd = Q->d_qdi;

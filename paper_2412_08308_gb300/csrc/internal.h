@@ -137,7 +137,7 @@ struct BandJob {
   int32_t q;        // query: its rows are cut into the bands; its row of scores is written
   int32_t packed;   // 1: a unit is two sequences in the 16-bit halves (pairs that cannot pass
                     //    the 16-bit range); 0: one sequence, int32 cells
-  int32_t nb;       // bands (band_rows() query rows each)
+  int32_t nb;       // bands (32 R query rows each)
   int32_t t_begin;  // first unit in BandArgs::tpos
   int32_t t_count;  // units of the stream, in order
   int32_t band0;    // global index of the job's band 0
@@ -161,10 +161,10 @@ struct BandArgs {
   int32_t *status;            // SW_ETIMEOUT on an expired wait
 };
 int band_threads();
-int band_rows();
-size_t band_smem_bytes();
-int band_max_ctas_per_sm();  // plan time: raises the shared-memory limit; 0 on failure
-cudaError_t launch_band(const BandArgs &a, int grid, cudaStream_t s);
+bool band_supported_R(int R);  // rows per lane: 8 or 16 (bands of 256 or 512 query rows)
+size_t band_smem_bytes(int R);
+int band_max_ctas_per_sm(int R);  // plan time: raises the shared-memory limit; 0 on failure
+cudaError_t launch_band(const BandArgs &a, int R, int grid, cudaStream_t s);
 
 // Traceback of selected hits (k_trace.cu): one warp per hit fills 4-bit
 // provenance codes per cell, one thread per hit walks them back.

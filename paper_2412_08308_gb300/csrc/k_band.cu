@@ -16,9 +16,10 @@
 //
 // Forms: int32 cells (one database sequence per unit, Algorithm 1's
 // statements) or two sequences per unit in the 16-bit halves of a word (only
-// for pairs that cannot pass the 16-bit range, so no rescue is needed).  Both
-// use split lanes: a lane's upper R/2 rows work on column c, its lower R/2
-// rows on column c - 1.
+// for pairs that cannot pass the 16-bit range, so no rescue is needed).  A
+// lane's R rows form one chain down the column (no split lanes: the pipeline
+// lag between consecutive bands is then 31 columns instead of 63, which
+// measured faster here, where several bands share each SM sub-partition).
 //
 // Rings and progress.  Each ring holds one 64-bit entry per column of the
 // job's whole stream, zeroed before the launch, and is written once: the
@@ -43,27 +44,31 @@ namespace swgb {
 namespace {
 
 constexpr int kBandStreamThreads = 256;  // 8 warps, one band at a time each
-constexpr int kBR = 8;                   // rows per lane: bands of 256 query rows
-constexpr int kBandRows = 32 * kBR;
-constexpr int kLagS = 2 * 32 - 1;        // split lanes: the last lane trails the first by 63 columns
-constexpr int kProfBytes = kProfRows * kBandRows;              // a band's profile: [21][32 lanes x R] bytes
-constexpr int kWarpBytes = ((kProfBytes + 320) + 127) / 128 * 128;  // + residues 2 x 32 B, boundary 2 x 16 x 8 B
+constexpr int kLag = 32 - 1;  // a band's last lane trails its first by 31 columns
 constexpr int kSubmatBytes = 512;
+// R rows per lane: bands of 32 R query rows; a band's profile is [21][32 lanes
+// x R] bytes, followed by its residue slots (2 x 32 B) and boundary slots (2 x
+// 16 x 8 B)
+template <int R>
+constexpr int kProfBytes = kProfRows * 32 * R;
+template <int R>
+constexpr int kWarpBytes = ((kProfBytes<R> + 320) + 127) / 128 * 128;
 
 // A band's profile in the warp's shared-memory block: byte [c][lane * R + r]
-// = SM(Q[row], c) for row = band * 256 + lane * R + r, the pad value for the
+// = SM(Q[row], c) for row = band * 32 R + lane * R + r, the pad value for the
 // pad residue (c = 20) and rows past the query's end.
+template <int R>
 __device__ __forceinline__ void build_band_profile(uint8_t *prof, const int8_t *sm, const uint8_t *q, int m,
                                                    int row0, int lane, int32_t pad) {
-  uint8_t codes[kBR];
+  uint8_t codes[R];
 #pragma unroll
-  for (int r = 0; r < kBR; ++r) {
-    const int row = row0 + lane * kBR + r;
+  for (int r = 0; r < R; ++r) {
+    const int row = row0 + lane * R + r;
     codes[r] = row < m ? q[row] : (uint8_t)kPadCode;
   }
   for (int c = 0; c < kProfRows; ++c) {
 #pragma unroll
-    for (int w = 0; w < kBR / 4; ++w) {
+    for (int w = 0; w < R / 4; ++w) {
       uint32_t v = 0;
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
@@ -71,21 +76,20 @@ __device__ __forceinline__ void build_band_profile(uint8_t *prof, const int8_t *
         const int32_t s = (c < kAlphabet && code < kAlphabet) ? (int32_t)sm[code * kAlphabet + c] : pad;
         v |= ((uint32_t)s & 0xffu) << (8 * b);
       }
-      *reinterpret_cast<uint32_t *>(prof + c * kBandRows + lane * kBR + 4 * w) = v;
+      *reinterpret_cast<uint32_t *>(prof + c * 32 * R + lane * R + 4 * w) = v;
     }
   }
 }
 
 // One band over one database unit (columns sbase .. sbase + npad - 1 of the
 // job's stream).  Returns false when a wait expired.
-template <int FORM>
+template <int R, int FORM>
 __device__ __forceinline__ bool band_unit(const BandArgs &a, const uint8_t *__restrict__ prof, uint8_t *ring,
                                           const int lane, const int posA, const int posB, const int64_t sbase,
                                           const unsigned long long *ring_in, unsigned long long *ring_out,
                                           const Consts &cs, Word<FORM> &Sout) {
   using W = Word<FORM>;
   constexpr bool PACKED = FORM == kFormPacked;
-  constexpr int R = kBR;
   const W H0 = (W)0;
   const W F0 = PACKED ? (W)cs.F0W : (W)0;
   const int npa = a.db.npad[posA];
@@ -93,7 +97,8 @@ __device__ __forceinline__ bool band_unit(const BandArgs &a, const uint8_t *__re
   const int npad = max(npa, npb);
   const uint8_t *resA = a.db.res + a.db.off[posA];
   const uint8_t *resB = a.db.res + a.db.off[posB];
-  const int nblk = (npad + kLagS + kColBlock - 1) / kColBlock;
+  constexpr int LAG = kLag;
+  const int nblk = (npad + LAG + kColBlock - 1) / kColBlock;
   const int nreal = npad / kColBlock;
   const bool prev = ring_in != nullptr, next = ring_out != nullptr;
   const bool lead = lane == 0;
@@ -103,9 +108,7 @@ __device__ __forceinline__ bool band_unit(const BandArgs &a, const uint8_t *__re
   LaneState<R, FORM> st;
   lane_reset(st, cs);
   W outH = H0, outF = F0, S = (W)0;
-  uint32_t outRes = kPadPair, prevRes = kPadPair;
-  // split lanes: the lower half's diagonal H, incoming H (int32) and F, best
-  W hdiagB = H0, midH = H0, midF = F0, S2 = (W)0;
+  uint32_t outRes = kPadPair;
   uint8_t *rres = ring;                              // [slot][2 seqs][16 B] residue codes
   uint2 *rgb = reinterpret_cast<uint2 *>(ring + 64);  // [slot][16] (H, F) of the band above
   const uint8_t *prow = prof + lane * R;
@@ -195,33 +198,10 @@ __device__ __forceinline__ bool band_unit(const BandArgs &a, const uint8_t *__re
           inH = (W)v.x;
           inF = (W)v.y;
         }
-        if constexpr (PACKED) {
-          uint32_t s1 = (uint32_t)S, s2 = (uint32_t)S2, hb = (uint32_t)hdiagB, mf = (uint32_t)midF, oh, of;
-          column_step_split<R, FORM>(st, hb, mf, prow, kBandRows, inRes, prevRes, (uint32_t)inH, (uint32_t)inF, cs,
-                                     s1, s2, oh, of, 0);
-          S = (W)s1;
-          S2 = (W)s2;
-          hdiagB = (W)hb;
-          midF = (W)mf;
-          outH = (W)oh;
-          outF = (W)of;
-        } else {
-          int32_t s1 = (int32_t)S, s2 = (int32_t)S2, hb = (int32_t)hdiagB, mh = (int32_t)midH, mf = (int32_t)midF;
-          int32_t oh, of;
-          column_step_split_int<R>(st, hb, mh, mf, prow, kBandRows, inRes, prevRes, (int32_t)inH, (int32_t)inF, cs,
-                                   s1, s2, oh, of);
-          S = (W)s1;
-          S2 = (W)s2;
-          hdiagB = (W)hb;
-          midH = (W)mh;
-          midF = (W)mf;
-          outH = (W)oh;
-          outF = (W)of;
-        }
-        outRes = prevRes;
-        prevRes = inRes;
+        column_step<R, FORM>(st, prow, 32 * R, inRes, inH, inF, cs, S, outH, outF, 0);
+        outRes = inRes;
         if (tail) {
-          const int j = t - kLagS;
+          const int j = t - LAG;
           if (j >= 0 && j < npad) {
             const uint32_t lo = (uint32_t)outH | 0x80000000u;
             st_relaxed_u64(ring_out + wpos, ((unsigned long long)(uint32_t)outF << 32) | lo);
@@ -244,16 +224,17 @@ __device__ __forceinline__ bool band_unit(const BandArgs &a, const uint8_t *__re
     }
   }
   if (lead) cp_async_wait<0>();
-  Sout = score_max<FORM>(S, S2);
+  Sout = S;
   return !failed;
 }
 
+template <int R>
 __global__ void __launch_bounds__(kBandStreamThreads, 2) band_stream_kernel(const BandArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   int8_t *sm = reinterpret_cast<int8_t *>(smem);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint8_t *prof = smem + kSubmatBytes + (size_t)warp * kWarpBytes;
-  uint8_t *ring = prof + kProfBytes;
+  uint8_t *prof = smem + kSubmatBytes + (size_t)warp * kWarpBytes<R>;
+  uint8_t *ring = prof + kProfBytes<R>;
   for (int i = threadIdx.x; i < kAlphabet * kAlphabet; i += blockDim.x) sm[i] = a.submat[i];
   __syncthreads();
   const Consts cs = make_consts(a.sc);
@@ -267,7 +248,7 @@ __global__ void __launch_bounds__(kBandStreamThreads, 2) band_stream_kernel(cons
     const int b = g - job.band0;
     const QDesc qd = a.qd[job.q];
     __syncwarp();
-    build_band_profile(prof, sm, a.qres + qd.qoff, qd.m, b * kBandRows, lane, a.sc.pad);
+    build_band_profile<R>(prof, sm, a.qres + qd.qoff, qd.m, b * 32 * R, lane, a.sc.pad);
     __syncwarp();
     const unsigned long long *ring_in = b > 0 ? a.rings + job.ring0 + (int64_t)(b - 1) * job.cols : nullptr;
     unsigned long long *ring_out = b + 1 < job.nb ? a.rings + job.ring0 + (int64_t)b * job.cols : nullptr;
@@ -278,7 +259,7 @@ __global__ void __launch_bounds__(kBandStreamThreads, 2) band_stream_kernel(cons
       const int2 p = a.tpos[job.t_begin + t];
       if (job.packed) {
         uint32_t S = 0u;
-        ok = band_unit<kFormPacked>(a, prof, ring, lane, p.x, p.y, sbase, ring_in, ring_out, cs, S);
+        ok = band_unit<R, kFormPacked>(a, prof, ring, lane, p.x, p.y, sbase, ring_in, ring_out, cs, S);
         for (int d = 16; d > 0; d >>= 1) S = __vmaxs2(S, __shfl_xor_sync(0xffffffffu, S, d));
         if (ok && lane == 0) {
           atomicMax(&orow[a.db.perm[p.x]], (int32_t)(S & 0xffffu));
@@ -287,7 +268,7 @@ __global__ void __launch_bounds__(kBandStreamThreads, 2) band_stream_kernel(cons
         sbase += max(a.db.npad[p.x], a.db.npad[p.y]);
       } else {
         int32_t S = 0;
-        ok = band_unit<kFormInt32>(a, prof, ring, lane, p.x, p.x, sbase, ring_in, ring_out, cs, S);
+        ok = band_unit<R, kFormInt32>(a, prof, ring, lane, p.x, p.x, sbase, ring_in, ring_out, cs, S);
         for (int d = 16; d > 0; d >>= 1) S = max(S, __shfl_xor_sync(0xffffffffu, S, d));
         if (ok && lane == 0) atomicMax(&orow[a.db.perm[p.x]], S);
         sbase += a.db.npad[p.x];
@@ -298,29 +279,38 @@ __global__ void __launch_bounds__(kBandStreamThreads, 2) band_stream_kernel(cons
   }
 }
 
-}  // namespace
+template <int R>
+size_t smem_of() {
+  return kSubmatBytes + (size_t)(kBandStreamThreads / 32) * kWarpBytes<R>;
+}
 
-int band_threads() { return kBandStreamThreads; }
-int band_rows() { return kBandRows; }
-size_t band_smem_bytes() { return kSubmatBytes + (size_t)(kBandStreamThreads / 32) * kWarpBytes; }
-
-int band_max_ctas_per_sm() {
-  if (cudaFuncSetAttribute(band_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)band_smem_bytes()) != cudaSuccess) {
+template <int R>
+int occupancy_of() {
+  if (cudaFuncSetAttribute(band_stream_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem_of<R>()) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, band_stream_kernel, kBandStreamThreads, band_smem_bytes()) !=
-      cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, band_stream_kernel<R>, kBandStreamThreads,
+                                                    smem_of<R>()) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   return n;
 }
 
-cudaError_t launch_band(const BandArgs &a, int grid, cudaStream_t s) {
-  band_stream_kernel<<<grid, kBandStreamThreads, band_smem_bytes(), s>>>(a);
+}  // namespace
+
+int band_threads() { return kBandStreamThreads; }
+bool band_supported_R(int R) { return R == 8 || R == 16; }
+size_t band_smem_bytes(int R) { return R == 16 ? smem_of<16>() : smem_of<8>(); }
+int band_max_ctas_per_sm(int R) { return R == 8 ? occupancy_of<8>() : R == 16 ? occupancy_of<16>() : 0; }
+
+cudaError_t launch_band(const BandArgs &a, int R, int grid, cudaStream_t s) {
+  if (R == 8) band_stream_kernel<8><<<grid, kBandStreamThreads, smem_of<8>(), s>>>(a);
+  else if (R == 16) band_stream_kernel<16><<<grid, kBandStreamThreads, smem_of<16>(), s>>>(a);
+  else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 

@@ -429,7 +429,8 @@ def test_bad_options_rejected(api):
     db = api.Database.from_sequences(db_s)
     bad_band = api.options()
     bad_band.band_stream = 3
-    for opts in (api.options(rows_per_lane=7), api.options(lanes_per_chain=3), api.options(intra_rows=12), bad_band):
+    for opts in (api.options(rows_per_lane=7), api.options(lanes_per_chain=3), api.options(intra_rows=12), bad_band,
+                 api.options(band_rows=12)):
         with pytest.raises(SwError) as e:
             api.PreparedQueries(db, q.residues, q.offsets, BLOSUM62, 10, 2, "packed", opts=opts)
         assert e.value.code == SW_EINVAL
@@ -495,18 +496,19 @@ def _band_db(seed, n, long_lens):
 
 
 @pytest.mark.parametrize("mode", MODES)
-@pytest.mark.parametrize("band", ["auto", "always"])
-def test_band_stream_ragged(api, mode, band):
-    # band-stream jobs (k_band.cu): queries across the band edges (256 rows a
-    # band: 511/512/513, 768/769 rows) and up to 12 bands, against a database
-    # with every padding edge and sequences at and past the cutover of 2,048
-    # residues (the queries below 512 rows meet those long units in one band
-    # each; the others every unit in their own band pipelines)
+@pytest.mark.parametrize("band,rows", [("auto", 0), ("always", 8), ("always", 16)])
+def test_band_stream_ragged(api, mode, band, rows):
+    # band-stream jobs (k_band.cu): queries across the band edges (8 rows a
+    # lane: 256-row bands, 511/512/513, 768/769 rows; 16 rows a lane: 512-row
+    # bands, 1023/1024/1025) and up to 12 bands, against a database with every
+    # padding edge and sequences at and past the cutover of 2,048 residues
+    # (the queries below two bands meet those long units in one band each;
+    # the others every unit in their own band pipelines)
     db = _band_db(511, 260, [2047, 2048, 2049, 3001, 5000])
     rng = np.random.Generator(np.random.PCG64(512))
-    ql = [0, 1, 144, 255, 256, 257, 511, 512, 513, 768, 769, 1500, 3000]
+    ql = [0, 1, 144, 255, 256, 257, 511, 512, 513, 768, 769, 1023, 1024, 1025, 1500, 3000]
     q = from_list([rng.integers(0, 20, size=L).astype(np.uint8) for L in ql])
-    got = _search(api, db, q, mode, opts=api.options(band_stream=band))
+    got = _search(api, db, q, mode, opts=api.options(band_stream=band, band_rows=rows))
     _assert_equal(got, oracle.scores(q, db, BLOSUM62, 10, 2))
 
 
