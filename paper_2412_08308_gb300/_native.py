@@ -74,6 +74,16 @@ def lib():
     return _lib
 
 
+def use_library(path):
+    """Bind every entry point of this module to the library at `path` (the
+    checked build libswgb_check.so, say) instead of libswgb.so.  Must come
+    before the first call in the process."""
+    global _lib
+    if _lib is not None:
+        raise RuntimeError("the library is already loaded in this process")
+    _lib = load(path)
+
+
 def check(rc):
     if rc != SW_OK:
         raise SwError(rc, lib().sw_last_error().decode())

@@ -4,6 +4,12 @@ Every translation unit under ``csrc/`` is compiled in parallel with nvcc
 (``-gencode arch=compute_103a,code=sm_103a -lineinfo -O3``) and linked into one
 shared library next to this file.  Rebuilds only when a source is newer than
 the library.
+
+``build(checked=True)`` builds ``libswgb_check.so`` instead, with
+``-DSW_CHECK``: its kernels test every index into a packed residue buffer, a
+profile, a boundary strip or ring and the scores before the access, record a
+status the host call reports, and skip the access (the stand-in for a memory
+checker, which this platform does not offer).
 """
 
 import os
@@ -16,6 +22,8 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libswgb.so")
 BUILD_DIR = os.path.join(HERE, "_build")
+CHECK_LIB = os.path.join(HERE, "libswgb_check.so")
+CHECK_BUILD_DIR = os.path.join(HERE, "_build_check")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 
@@ -31,23 +39,27 @@ def _deps():
     return deps
 
 
-def up_to_date():
-    if not os.path.exists(LIB):
+def up_to_date(lib=LIB):
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force=False, verbose=False):
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD_DIR, exist_ok=True)
+def build(force=False, verbose=False, checked=False):
+    lib = CHECK_LIB if checked else LIB
+    build_dir = CHECK_BUILD_DIR if checked else BUILD_DIR
+    if not force and up_to_date(lib):
+        return lib
+    os.makedirs(build_dir, exist_ok=True)
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
+    if checked:
+        flags += ["-DSW_CHECK"]
     if verbose:
         flags += ["-Xptxas", "-v"]
 
     def compile_one(src):
-        obj = os.path.join(BUILD_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         cmd = [NVCC] + flags + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -58,15 +70,14 @@ def build(force=False, verbose=False):
 
     with ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
         objs = list(ex.map(compile_one, sources()))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose="-v" in sys.argv)
-    print(LIB)
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, checked="--checked" in sys.argv))

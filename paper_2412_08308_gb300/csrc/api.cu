@@ -5,9 +5,12 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <numeric>
 #include <string>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/swgb.h"
 #include "internal.h"
@@ -15,6 +18,13 @@
 using namespace swgb;
 
 namespace {
+
+// NVTX range around the host-side enqueue of one stage of a search (profile,
+// DP kernels, rescue), for timeline tools; free when no tool is attached.
+struct StageRange {
+  explicit StageRange(const char *name) { nvtxRangePushA(name); }
+  ~StageRange() { nvtxRangePop(); }
+};
 
 thread_local std::string g_err;
 
@@ -99,7 +109,7 @@ struct sw_queries {
   std::vector<QDesc> qd, qdi;  // inter-task and intra-task plans per query
   std::vector<QDesc> qdp;      // query-track plans (packed mode, inter-task kernel)
   std::vector<TrackChunk> track;  // their chunk descriptors
-  int64_t n_units = 0, n_long = 0;
+  int64_t n_units = 0, n_long = 0, n_upos = 0, n_ipos32 = 0;
   int64_t n_tasks = 0, n_itasks = 0, n_itasks32 = 0, n_rtask_cap = 0;
   int64_t npairs = 0, n_ptasks = 0, n_solo = 0, n_single = 0;
   bool inter_may_flag = false;  // some packed inter-task pair can exceed the 16-bit threshold
@@ -271,6 +281,7 @@ int sw_db_prepare(const uint8_t *residues, const int64_t *offsets, int64_t n_seq
   db->view.len = (const int32_t *)(p + b_res + b_off + b_i32);
   db->view.perm = (const int32_t *)(p + b_res + b_off + 2 * b_i32);
   db->view.n = n_seqs;
+  db->view.res_bytes = (int64_t)packed.size();
   db->d_ident = (const int32_t *)(p + b_res + b_off + 3 * b_i32);
   std::vector<int32_t> ident((size_t)n_seqs + 1);
   for (int64_t k = 0; k <= n_seqs; ++k) ident[k] = (int32_t)std::max<int64_t>(0, std::min<int64_t>(k, n_seqs - 1));
@@ -842,6 +853,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   Q->n_tasks = (int64_t)tw.size();
   Q->n_itasks = (int64_t)twi.size();
   Q->n_itasks32 = (int64_t)twi32.size();
+  Q->n_ipos32 = (int64_t)ipos32.size();
   Q->long_stride = std::max<int64_t>(1, packed ? 2 * n_long : n_long);
   Q->n_rtask_cap = Q->inter_may_flag ? rcap : 0;
 
@@ -943,6 +955,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   Q->d_btpos = (int2 *)take(b_btpos);
   Q->d_brings = Q->n_bjobs ? (unsigned long long *)take(b_brings) : nullptr;
   Q->d_upos = const_cast<int32_t *>(db->d_ident) + s0;  // the short sequences, in sorted order
+  Q->n_upos = n + 1 - s0;
 
   std::vector<Task> tasks(Q->n_tasks), itasks(Q->n_itasks), itasks32(Q->n_itasks32), ptasks(Q->n_ptasks);
   for (int64_t i = 0; i < Q->n_ptasks; ++i) ptasks[i] = twp[i].t;
@@ -1028,6 +1041,7 @@ int sw_search_prepared(const sw_db *db, const sw_queries *Q, int32_t *scores_dev
   int32_t *w = Q->d_words;
 
   SW_CUDA(cudaMemsetAsync(w, 0, 4 * Q->zero_words(), s), "memset");
+  std::unique_ptr<StageRange> stage(new StageRange("swgb: query profiles"));
   if (Q->n_solo)
     SW_CUDA(launch_build_profiles(Q->d_qres, Q->d_qd, nq, Q->d_submat, Q->sc.pad, Q->d_prof, s), "profile kernel");
   if (Q->npairs)
@@ -1038,6 +1052,7 @@ int sw_search_prepared(const sw_db *db, const sw_queries *Q, int32_t *scores_dev
     SW_CUDA(launch_build_profiles(Q->d_qres, Q->d_qdi, nq, Q->d_submat, Q->sc.pad, Q->d_prof, s),
             "profile kernel");
 
+  stage.reset(new StageRange("swgb: dynamic programming"));
   // band-stream jobs add their scores with atomicMax: every score starts at 0
   if (Q->n_bjobs) SW_CUDA(cudaMemsetAsync(scores_dev, 0, 4 * (size_t)Q->nq * (size_t)db->n, s), "memset");
   const bool band_timing = Q->timing && Q->n_bjobs;
@@ -1046,9 +1061,12 @@ int sw_search_prepared(const sw_db *db, const sw_queries *Q, int32_t *scores_dev
   InterArgs a{};
   a.db = db->view;
   a.unit_pos = db->d_ident;
+  a.n_unit_pos = db->n + 1;
   a.prof = Q->d_prof;
+  a.prof_bytes = Q->prof_bytes;
   a.out = scores_dev;
   a.out_stride = db->n;
+  a.out_size = Q->nq * db->n;
   a.sc = Q->sc;
   a.status = w + 2;
 
@@ -1075,6 +1093,9 @@ int sw_search_prepared(const sw_db *db, const sw_queries *Q, int32_t *scores_dev
       ba.rings = Q->d_brings;
       ba.out = scores_dev;
       ba.out_stride = db->n;
+      ba.out_size = Q->nq * db->n;
+      ba.ring_entries = Q->band_ring_bytes / 8;
+      ba.n_tpos = Q->n_btargets;
       ba.sc = Q->sc;
       ba.status = w + 2;
       SW_CUDA(launch_band(ba, Q->bR, Q->bgrid, Q->side), "band-stream kernel");
@@ -1087,6 +1108,7 @@ int sw_search_prepared(const sw_db *db, const sw_queries *Q, int32_t *scores_dev
     b.flag_count = w + 8 + nq;
     b.flag_pos = Q->d_iflag_pos;
     b.flag_stride = Q->long_stride;
+    b.flag_size = Q->nq * Q->long_stride;
     if (Q->n_itasks) {  // packed units that cannot saturate
       b.tasks = Q->d_itasks;
       b.n_tasks = w + Q->zero_words() + 1;
@@ -1095,6 +1117,7 @@ int sw_search_prepared(const sw_db *db, const sw_queries *Q, int32_t *scores_dev
     }
     if (Q->n_itasks32) {  // single sequences in int32
       b.unit_pos = Q->d_ipos32;
+      b.n_unit_pos = Q->n_ipos32;
       b.tasks = Q->d_itasks32;
       b.n_tasks = w + Q->zero_words() + 2;
       b.task_counter = w + 5;
@@ -1115,6 +1138,7 @@ int sw_search_prepared(const sw_db *db, const sw_queries *Q, int32_t *scores_dev
     p.qd = Q->d_qdp;
     p.track = Q->d_track;
     p.unit_pos = Q->d_upos;
+    p.n_unit_pos = Q->n_upos;
     p.tasks = Q->d_ptasks;
     p.n_tasks = w + Q->zero_words() + 3;
     p.task_counter = w + 6;
@@ -1139,6 +1163,7 @@ int sw_search_prepared(const sw_db *db, const sw_queries *Q, int32_t *scores_dev
     a.flag_count = w + 8;
     a.flag_pos = Q->d_flag_pos;
     a.flag_stride = db->n;
+    a.flag_size = Q->inter_may_flag ? Q->nq * db->n : 0;
     SW_CUDA(launch_inter(a, Q->R, packed ? kFormPacked : kFormInt32, Q->grid, threads, Q->smem, s), "inter-task kernel");
   }
   if (Q->timing && !band_timing && (Q->n_tasks || Q->n_ptasks)) {
@@ -1147,10 +1172,12 @@ int sw_search_prepared(const sw_db *db, const sw_queries *Q, int32_t *scores_dev
   }
   if (Q->n_tasks) {
     if (Q->inter_may_flag) {
+      stage.reset(new StageRange("swgb: int32 rescue"));
       SW_CUDA(launch_rescue_tasks(w + 8, Q->d_qd, nq, db->n, threads / 32, 0, Q->d_rtasks, w + 3, w + 1, s),
               "rescue task kernel");
       InterArgs r = a;
       r.unit_pos = Q->d_flag_pos;
+      r.n_unit_pos = Q->nq * db->n;
       r.tasks = Q->d_rtasks;
       r.n_tasks = w + 3;
       r.task_counter = w + 1;
@@ -1219,6 +1246,7 @@ int sw_queries_status(const sw_queries *Q, void *stream, int64_t *rescued) {
   if (rescued) *rescued = inter_flags;
   if (w[2] == SW_ETIMEOUT) return fail(SW_ETIMEOUT, "a bounded device wait expired");
   if (w[2] == kStatusSaturated) return fail(SW_ECUDA, "internal error: a query-pair lane passed its bound");
+  if (w[2] == kStatusBounds) return fail(SW_ECUDA, "internal error: an index left its buffer (checked build)");
   if (intra_flags) return fail(SW_ECUDA, "internal error: a packed intra-task lane passed its bound");
   return SW_OK;
 }

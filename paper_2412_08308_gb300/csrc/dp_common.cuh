@@ -22,6 +22,46 @@ namespace swgb {
 
 constexpr uint32_t kPadPair = 20u | (20u << 16);
 
+// Checked build (-DSW_CHECK): every index into a packed residue buffer, a
+// profile, a boundary strip or ring, or an output is tested before the
+// access; an index outside its buffer records kStatusBounds in the status
+// word and the access is skipped (no trap, no assert).  The regular build
+// compiles the tests away.
+#ifdef SW_CHECK
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+
+__device__ __forceinline__ bool in_range(int64_t i, int64_t n, int32_t *status) {
+  if constexpr (kChecked) {
+    if (i < 0 || i >= n) {
+      atomicExch(status, kStatusBounds);
+      return false;
+    }
+  }
+  return true;
+}
+
+// Profile row codes of a column (0..20, 20 = pad), as the form reads them:
+// the low byte (int32 forms), the two 16-bit halves (two sequences per word)
+// or the whole word (query pairs, one bare code).  A code past the pad row is
+// reported and replaced by the pad code.
+template <int FORM>
+__device__ __forceinline__ uint32_t checked_codes(uint32_t res, int32_t *status) {
+  if constexpr (kChecked) {
+    bool bad;
+    if constexpr (FORM == kFormPacked) bad = (res & 0xffffu) > (uint32_t)kPadCode || (res >> 16) > (uint32_t)kPadCode;
+    else if constexpr (FORM == kFormQPair) bad = res > (uint32_t)kPadCode;
+    else bad = (res & 0xffu) > (uint32_t)kPadCode;
+    if (bad) {
+      atomicExch(status, kStatusBounds);
+      return FORM == kFormPacked ? kPadPair : (uint32_t)kPadCode;
+    }
+  }
+  return res;
+}
+
 struct Consts {
   // packed: (x, x) in both 16-bit halves
   uint32_t goW, geW, F0W, E0W;
@@ -351,22 +391,23 @@ __device__ __forceinline__ void write_scores(Word<FORM> S, int posA, int posB, i
   int32_t *flag_pos = a.flag_pos;
   const int64_t row = (int64_t)q * a.out_stride;
   const int64_t frow = (int64_t)q * a.flag_stride;
+  if (!in_range(posA, db.n, a.status) || !in_range(posB, db.n, a.status)) return;
   if constexpr (PACKED) {
     const int32_t sa = (int32_t)((uint32_t)S & 0xffffu), sb = (int32_t)((uint32_t)S >> 16);
     if (sa > sc.thresh) {
       const int i = atomicAdd(&flag_count[q], 1);
-      flag_pos[frow + i] = posA;
+      if (in_range(frow + i, a.flag_size, a.status)) flag_pos[frow + i] = posA;
     }
-    out[row + db.perm[posA]] = sa;
+    if (in_range(row + db.perm[posA], a.out_size, a.status)) out[row + db.perm[posA]] = sa;
     if (posB != posA) {
       if (sb > sc.thresh) {
         const int i = atomicAdd(&flag_count[q], 1);
-        flag_pos[frow + i] = posB;
+        if (in_range(frow + i, a.flag_size, a.status)) flag_pos[frow + i] = posB;
       }
-      out[row + db.perm[posB]] = sb;
+      if (in_range(row + db.perm[posB], a.out_size, a.status)) out[row + db.perm[posB]] = sb;
     }
   } else {
-    out[row + db.perm[posA]] = (int32_t)S;
+    if (in_range(row + db.perm[posA], a.out_size, a.status)) out[row + db.perm[posA]] = (int32_t)S;
   }
 }
 

@@ -67,6 +67,7 @@ constexpr int kFormInt32 = 0;   // one database sequence per chain, 32-bit cells
 constexpr int kFormPacked = 1;  // two database sequences per chain, 16-bit halves
 constexpr int kFormQPair = 2;   // two queries per chain (one sequence), 16-bit halves
 constexpr int32_t kStatusSaturated = 100;  // device status: a lane that could not saturate did
+constexpr int32_t kStatusBounds = 101;     // device status (checked build): an index left its buffer
 
 // A unit of DP work for one chain: one database sequence (int32 form) or
 // two (packed form), given as positions in the length-sorted database.
@@ -79,6 +80,7 @@ struct Task {
 
 struct DbView {
   const uint8_t *res;   // packed residues, sorted order
+  int64_t res_bytes;    // bytes of the packed residue buffer
   const int64_t *off;   // [n] byte offset of sorted sequence k (16-byte aligned)
   const int32_t *npad;  // [n] padded length (multiple of 16, >= kMinPad)
   const int32_t *len;   // [n] true length
@@ -106,6 +108,11 @@ struct InterArgs {
   int64_t flag_stride;
   Scoring sc;
   int32_t *status;          // device status word (SW_ETIMEOUT on an expired wait)
+  // buffer sizes, tested by the checked build (-DSW_CHECK) before every access
+  int64_t prof_bytes;       // bytes of `prof`
+  int64_t out_size;         // entries of `out`
+  int64_t n_unit_pos;       // entries of `unit_pos`
+  int64_t flag_size;        // entries of `flag_pos`
 };
 
 // Arguments of the pair-band kernel (k_pair.cu): one long pair, int32 cells,
@@ -159,6 +166,10 @@ struct BandArgs {
   int64_t out_stride;
   Scoring sc;
   int32_t *status;            // SW_ETIMEOUT on an expired wait
+  // buffer sizes, tested by the checked build (-DSW_CHECK) before every access
+  int64_t ring_entries;       // entries of `rings`
+  int64_t out_size;           // entries of `out`
+  int64_t n_tpos;             // entries of `tpos`
 };
 int band_threads();
 bool band_supported_R(int R);  // rows per lane: 8 or 16 (bands of 256 or 512 query rows)

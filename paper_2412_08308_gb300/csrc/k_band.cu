@@ -117,10 +117,10 @@ __device__ __forceinline__ bool band_unit(const BandArgs &a, const uint8_t *__re
   auto prefetch = [&](int blk) {
     uint8_t *d = rres + (blk & 1) * 32;
     const int col = blk * kColBlock;
-    if (col < npa) cp_async16(d, resA + col);
+    if (col < npa && in_range(resA + col + 15 - a.db.res, a.db.res_bytes, a.status)) cp_async16(d, resA + col);
     else *reinterpret_cast<uint4 *>(d) = make_uint4(0x14141414u, 0x14141414u, 0x14141414u, 0x14141414u);
     if (PACKED) {
-      if (col < npb) cp_async16(d + 16, resB + col);
+      if (col < npb && in_range(resB + col + 15 - a.db.res, a.db.res_bytes, a.status)) cp_async16(d + 16, resB + col);
       else *reinterpret_cast<uint4 *>(d + 16) = make_uint4(0x14141414u, 0x14141414u, 0x14141414u, 0x14141414u);
     }
     cp_async_commit();
@@ -134,7 +134,8 @@ __device__ __forceinline__ bool band_unit(const BandArgs &a, const uint8_t *__re
   int64_t rpos = sbase;
   unsigned long long pend = 0ull;
   auto load = [&]() {
-    if (lane < kColBlock) pend = ld_relaxed_u64(ring_in + rpos + lane);
+    if (lane < kColBlock && in_range(ring_in - a.rings + rpos + lane, a.ring_entries, a.status))
+      pend = ld_relaxed_u64(ring_in + rpos + lane);
   };
   // wait until the loaded entries are written, unpack them into `slot`, advance
   auto land = [&](int slot) {
@@ -153,7 +154,8 @@ __device__ __forceinline__ bool band_unit(const BandArgs &a, const uint8_t *__re
       }
       if (!ok) {
         __nanosleep(32);  // (a waiting band leaves the issue slots to the bands that compute)
-        pend = ld_relaxed_u64(ring_in + rpos + lane);
+        if (in_range(ring_in - a.rings + rpos + lane, a.ring_entries, a.status))
+          pend = ld_relaxed_u64(ring_in + rpos + lane);
         ok = (pend >> 31 & 1ull) != 0ull;
       }
     }
@@ -198,11 +200,12 @@ __device__ __forceinline__ bool band_unit(const BandArgs &a, const uint8_t *__re
           inH = (W)v.x;
           inF = (W)v.y;
         }
+        if constexpr (kChecked) inRes = checked_codes<FORM>(inRes, a.status);
         column_step<R, FORM>(st, prow, 32 * R, inRes, inH, inF, cs, S, outH, outF, 0);
         outRes = inRes;
         if (tail) {
           const int j = t - LAG;
-          if (j >= 0 && j < npad) {
+          if (j >= 0 && j < npad && in_range(ring_out - a.rings + wpos, a.ring_entries, a.status)) {
             const uint32_t lo = (uint32_t)outH | 0x80000000u;
             st_relaxed_u64(ring_out + wpos, ((unsigned long long)(uint32_t)outF << 32) | lo);
             ++wpos;
@@ -256,21 +259,26 @@ __global__ void __launch_bounds__(kBandStreamThreads, 2) band_stream_kernel(cons
     int64_t sbase = 0;
     bool ok = true;
     for (int t = 0; t < job.t_count && ok; ++t) {
-      const int2 p = a.tpos[job.t_begin + t];
+      int2 p = make_int2(0, 0);
+      if (in_range(job.t_begin + t, a.n_tpos, a.status)) p = a.tpos[job.t_begin + t];
+      if (!in_range(p.x, a.db.n, a.status) || !in_range(p.y, a.db.n, a.status)) p = make_int2(0, 0);
       if (job.packed) {
         uint32_t S = 0u;
         ok = band_unit<R, kFormPacked>(a, prof, ring, lane, p.x, p.y, sbase, ring_in, ring_out, cs, S);
         for (int d = 16; d > 0; d >>= 1) S = __vmaxs2(S, __shfl_xor_sync(0xffffffffu, S, d));
         if (ok && lane == 0) {
-          atomicMax(&orow[a.db.perm[p.x]], (int32_t)(S & 0xffffu));
-          if (p.y != p.x) atomicMax(&orow[a.db.perm[p.y]], (int32_t)(S >> 16));
+          if (in_range(job.q * a.out_stride + a.db.perm[p.x], a.out_size, a.status))
+            atomicMax(&orow[a.db.perm[p.x]], (int32_t)(S & 0xffffu));
+          if (p.y != p.x && in_range(job.q * a.out_stride + a.db.perm[p.y], a.out_size, a.status))
+            atomicMax(&orow[a.db.perm[p.y]], (int32_t)(S >> 16));
         }
         sbase += max(a.db.npad[p.x], a.db.npad[p.y]);
       } else {
         int32_t S = 0;
         ok = band_unit<R, kFormInt32>(a, prof, ring, lane, p.x, p.x, sbase, ring_in, ring_out, cs, S);
         for (int d = 16; d > 0; d >>= 1) S = max(S, __shfl_xor_sync(0xffffffffu, S, d));
-        if (ok && lane == 0) atomicMax(&orow[a.db.perm[p.x]], S);
+        if (ok && lane == 0 && in_range(job.q * a.out_stride + a.db.perm[p.x], a.out_size, a.status))
+          atomicMax(&orow[a.db.perm[p.x]], S);
         sbase += a.db.npad[p.x];
       }
     }

@@ -66,7 +66,9 @@ __device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, cons
                                            const int npad, const int npa, const int npb,
                                            const uint8_t *__restrict__ resA, const uint8_t *__restrict__ resB,
                                            uint8_t *ring, uint2 *gb, const bool prev, const bool next,
-                                           const uint32_t restart, const Consts &cs, Word<FORM> &S) {
+                                           const uint32_t restart, const Consts &cs, Word<FORM> &S,
+                                           const uint8_t *res0, const int64_t res_bytes, const int gb_len,
+                                           int32_t *status) {
   using W = Word<FORM>;
   constexpr bool PACKED = FORM != kFormInt32;      // 16-bit halves
   constexpr bool PAIRS = FORM == kFormPacked;      // two database sequences per unit
@@ -93,13 +95,13 @@ __device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, cons
     const int slot = blk & 1;
     const int col = blk * kColBlock;
     uint8_t *d = rres + slot * 32;
-    if (col < npa) cp_async16(d, resA + col);
+    if (col < npa && in_range(resA + col + 15 - res0, res_bytes, status)) cp_async16(d, resA + col);
     else *reinterpret_cast<uint4 *>(d) = make_uint4(0x14141414u, 0x14141414u, 0x14141414u, 0x14141414u);
     if (PAIRS) {
-      if (col < npb) cp_async16(d + 16, resB + col);
+      if (col < npb && in_range(resB + col + 15 - res0, res_bytes, status)) cp_async16(d + 16, resB + col);
       else *reinterpret_cast<uint4 *>(d + 16) = make_uint4(0x14141414u, 0x14141414u, 0x14141414u, 0x14141414u);
     }
-    if (prev && col < npad) {
+    if (prev && col < npad && in_range(col + 15, gb_len, status)) {
 #pragma unroll
       for (int i = 0; i < 8; ++i) cp_async16(rgb + slot * 16 + 2 * i, gb + col + 2 * i);
     } else {
@@ -154,6 +156,7 @@ __device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, cons
           inH = (W)v.x;
           inF = (W)v.y;
         }
+        if constexpr (kChecked) inRes = checked_codes<FORM>(inRes, status);
         if constexpr (SPLIT) {
           uint32_t s = (uint32_t)S, oh, of;
           column_step_split<R, FORM>(st, hdiagB, midF, prow, stride, inRes, prevRes, (uint32_t)inH, (uint32_t)inF,
@@ -169,7 +172,8 @@ __device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, cons
         }
         if (tail) {
           const int j = t - chain_lag<R, FORM>(L);
-          if ((unsigned)j < (unsigned)npad) gb[j] = make_uint2((uint32_t)outH, (uint32_t)outF);
+          if ((unsigned)j < (unsigned)npad && in_range(j, gb_len, status))
+            gb[j] = make_uint2((uint32_t)outH, (uint32_t)outF);
         }
       }
     }
@@ -226,8 +230,12 @@ __global__ void __launch_bounds__(kThreads, 2) inter_kernel(const InterArgs a) {
     int posA = 0, posB = 0, npa = 0, npb = 0;
     if (live) {
       const int u = tk.unit_begin + ci;
-      posA = a.unit_pos[PAIRS ? 2 * u : u];
-      posB = PAIRS ? a.unit_pos[2 * u + 1] : posA;
+      const int iB = PAIRS ? 2 * u + 1 : u;
+      if (in_range(iB, a.n_unit_pos, a.status)) {
+        posA = a.unit_pos[PAIRS ? 2 * u : u];
+        posB = PAIRS ? a.unit_pos[iB] : posA;
+      }
+      if (!in_range(posA, a.db.n, a.status) || !in_range(posB, a.db.n, a.status)) posA = posB = 0;
       npa = a.db.npad[posA];
       npb = PAIRS ? a.db.npad[posB] : 0;
     }
@@ -242,6 +250,11 @@ __global__ void __launch_bounds__(kThreads, 2) inter_kernel(const InterArgs a) {
 
     auto issue = [&](int c) {
       const int b = dbl ? (c & 1) : 0;
+      const int64_t end = qd.prof_off + (int64_t)(c + 1) * qd.chunk_bytes;
+      if (!in_range(end - 1, a.prof_bytes, a.status) || (kChecked && qd.chunk_bytes > a.pbuf_bytes)) {
+        mbar_arrive_expect_tx(&mbar[b], 0u);  // (checked build: the copy is skipped, the phase completes)
+        return;
+      }
       mbar_arrive_expect_tx(&mbar[b], (uint32_t)qd.chunk_bytes);
       bulk_g2s(pbuf + b * a.pbuf_bytes, a.prof + qd.prof_off + (int64_t)c * qd.chunk_bytes,
                (uint32_t)qd.chunk_bytes, &mbar[b]);
@@ -268,7 +281,8 @@ __global__ void __launch_bounds__(kThreads, 2) inter_kernel(const InterArgs a) {
         return;
       }
       chain_pass<R, FORM>(pbuf + b * a.pbuf_bytes, qd.chunk_stride, L, k, lane, slot, gstride, live, nblk, npad,
-                          npa, npb, resA, resB, ring, gb, c > 0, c + 1 < qd.nchunks, restart, cs, S);
+                          npa, npb, resA, resB, ring, gb, c > 0, c + 1 < qd.nchunks, restart, cs, S,
+                          a.db.res, a.db.res_bytes, a.gbuf_stride, a.status);
       __syncthreads();
       // the buffer just used is free: load the chunk after the one in flight
       // (one buffer: the next chunk, while the other CTA on this SM computes)
@@ -284,8 +298,9 @@ __global__ void __launch_bounds__(kThreads, 2) inter_kernel(const InterArgs a) {
           if (live && k == 0) {
             const int32_t sa = (int32_t)((uint32_t)m & 0xffffu), sb = (int32_t)((uint32_t)m >> 16);
             const int32_t p = a.db.perm[posA];
-            if (endA) a.out[(int64_t)tc.qa * a.out_stride + p] = sa;
-            if (endB) a.out[(int64_t)tc.qb * a.out_stride + p] = sb;
+            const int64_t ia = (int64_t)tc.qa * a.out_stride + p, ib = (int64_t)tc.qb * a.out_stride + p;
+            if (endA && in_range(ia, a.out_size, a.status)) a.out[ia] = sa;
+            if (endB && in_range(ib, a.out_size, a.status)) a.out[ib] = sb;
             if ((endA && sa > a.sc.thresh) || (endB && sb > a.sc.thresh)) atomicExch(a.status, kStatusSaturated);
           }
           S = (W)((uint32_t)S & ~(((tc.flags & kEndA) ? 0x0000ffffu : 0u) | ((tc.flags & kEndB) ? 0xffff0000u : 0u)));

@@ -56,7 +56,8 @@ __device__ __forceinline__ void sweep_chunk(IntraShared *sh, const uint8_t *pbuf
                                             uint4 *rings, const int Wq, const int warp, const int lane,
                                             const uint8_t *resA, const uint8_t *resB, const int npa, const int npb,
                                             const int npad, const bool prev, const bool next, uint2 *gb,
-                                            int32_t *status, const Consts &cs, Word<FORM> &S) {
+                                            int32_t *status, const Consts &cs, Word<FORM> &S,
+                                            const uint8_t *res0, const int64_t res_bytes, const int gb_len) {
   using W = Word<FORM>;
   constexpr bool PACKED = FORM != kFormInt32;
   // split lanes (two half-chains a column apart): a warp's last lane trails
@@ -87,10 +88,14 @@ __device__ __forceinline__ void sweep_chunk(IntraShared *sh, const uint8_t *pbuf
   uint2 gvn = make_uint2(0u, 0u);
   auto fetch = [&](int col) {
     if (lane == 0 && col < npad) {
-      ra4n = col < npa ? *reinterpret_cast<const uint4 *>(resA + col) : padv;
-      if (PACKED) rb4n = col < npb ? *reinterpret_cast<const uint4 *>(resB + col) : padv;
+      ra4n = col < npa && in_range(resA + col + 15 - res0, res_bytes, status)
+                 ? *reinterpret_cast<const uint4 *>(resA + col) : padv;
+      if (PACKED)
+        rb4n = col < npb && in_range(resB + col + 15 - res0, res_bytes, status)
+                   ? *reinterpret_cast<const uint4 *>(resB + col) : padv;
     }
-    if (prev && lane < kColBlock && col + lane < npad) gvn = __ldcg(gb + col + lane);
+    if (prev && lane < kColBlock && col + lane < npad && in_range(col + lane, gb_len, status))
+      gvn = __ldcg(gb + col + lane);
   };
   if (first) fetch(0);
   for (int blk = 0; blk < nblk; ++blk) {
@@ -149,6 +154,7 @@ __device__ __forceinline__ void sweep_chunk(IntraShared *sh, const uint8_t *pbuf
             inRes = v.z;
           }
         }
+        if constexpr (kChecked) inRes = checked_codes<FORM>(inRes, status);
         if constexpr (PACKED) {
           uint32_t s = (uint32_t)S, s2 = (uint32_t)S2, hb = (uint32_t)hdiagB, mf = (uint32_t)midF, oh, of;
           column_step_split<R, FORM>(st, hb, mf, prow, chunk_stride, inRes, prevRes, (uint32_t)inH, (uint32_t)inF,
@@ -178,7 +184,7 @@ __device__ __forceinline__ void sweep_chunk(IntraShared *sh, const uint8_t *pbuf
           const int col = tau - LAG;
           if (col >= 0 && col < npad) {
             if (!last) ring_out[col % kRing] = make_uint4((uint32_t)outH, (uint32_t)outF, outRes, 0u);
-            else if (next) gb[col] = make_uint2((uint32_t)outH, (uint32_t)outF);
+            else if (next && in_range(col, gb_len, status)) gb[col] = make_uint2((uint32_t)outH, (uint32_t)outF);
           }
         }
       }
@@ -226,8 +232,12 @@ __global__ void __launch_bounds__(kIntraThreads, 1) intra_kernel(const InterArgs
     const QDesc qd = a.qd[tk.q];
     const int Wq = qd.L / 32;  // warps of the chain for this query
     const int u = tk.unit_begin;
-    const int posA = a.unit_pos[PACKED ? 2 * u : u];
-    const int posB = PACKED ? a.unit_pos[2 * u + 1] : posA;
+    int posA = 0, posB = 0;
+    if (in_range(PACKED ? 2 * u + 1 : u, a.n_unit_pos, a.status)) {
+      posA = a.unit_pos[PACKED ? 2 * u : u];
+      posB = PACKED ? a.unit_pos[2 * u + 1] : posA;
+    }
+    if (!in_range(posA, a.db.n, a.status) || !in_range(posB, a.db.n, a.status)) posA = posB = 0;
     const int npa = a.db.npad[posA];
     const int npb = PACKED ? a.db.npad[posB] : 0;
     const int npad = max(npa, npb);
@@ -242,8 +252,13 @@ __global__ void __launch_bounds__(kIntraThreads, 1) intra_kernel(const InterArgs
         sh->cons[threadIdx.x] = 0;
       }
       if (threadIdx.x == 0) {
-        mbar_arrive_expect_tx(&sh->mbar, (uint32_t)qd.chunk_bytes);
-        bulk_g2s(pbuf, a.prof + qd.prof_off + (int64_t)c * qd.chunk_bytes, (uint32_t)qd.chunk_bytes, &sh->mbar);
+        if (in_range(qd.prof_off + (int64_t)(c + 1) * qd.chunk_bytes - 1, a.prof_bytes, a.status) &&
+            (!kChecked || qd.chunk_bytes <= a.pbuf_bytes)) {
+          mbar_arrive_expect_tx(&sh->mbar, (uint32_t)qd.chunk_bytes);
+          bulk_g2s(pbuf, a.prof + qd.prof_off + (int64_t)c * qd.chunk_bytes, (uint32_t)qd.chunk_bytes, &sh->mbar);
+        } else {
+          mbar_arrive_expect_tx(&sh->mbar, 0u);  // (checked build: the copy is skipped, the phase completes)
+        }
       }
       __syncthreads();
       const bool ok = mbar_wait_bounded(&sh->mbar, parity);
@@ -254,7 +269,7 @@ __global__ void __launch_bounds__(kIntraThreads, 1) intra_kernel(const InterArgs
       }
       if (warp < Wq)
         sweep_chunk<R, FORM>(sh, pbuf, qd.chunk_stride, rings, Wq, warp, lane, resA, resB, npa, npb, npad, c > 0,
-                             c + 1 < qd.nchunks, gb, a.status, cs, S);
+                             c + 1 < qd.nchunks, gb, a.status, cs, S, a.db.res, a.db.res_bytes, a.gbuf_stride);
       __syncthreads();  // chunk done: ring counters, strip and profile buffer are free
       if (*vabort) return;
     }

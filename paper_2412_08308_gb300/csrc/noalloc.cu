@@ -192,6 +192,9 @@ extern "C" int sw_search_noalloc(const sw_db *db, const uint8_t *query, int64_t 
   InterArgs a{};
   a.db = v;
   a.unit_pos = db_ident(db);  // the database's own [0, 1, ..., n - 1]: unit u is sorted position u
+  a.n_unit_pos = n + 1;
+  a.prof_bytes = (int64_t)kProfMax;
+  a.out_size = n;
   a.qd = reinterpret_cast<const QDesc *>(scr + kOffQDesc);
   a.tasks = tasks;
   a.n_tasks = words + 1;
@@ -218,5 +221,6 @@ extern "C" int sw_search_noalloc(const sw_db *db, const uint8_t *query, int64_t 
     return cuda_err(e, "status read");
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_err(e, "synchronise");
   if (status == SW_ETIMEOUT) return fail_msg(SW_ETIMEOUT, "sw_search_noalloc: a bounded device wait expired");
+  if (status == kStatusBounds) return fail_msg(SW_ECUDA, "sw_search_noalloc: an index check failed (checked build)");
   return SW_OK;
 }

@@ -1,9 +1,11 @@
 """The N > 1 host path of bench.py on CPU: two gloo ranks, no GPU.
 
-bench.py runs one process per GPU with no data-path collective (each rank
-searches its own resident copy: weak scaling).  The only communication is a
-barrier and the max-reduction of the elapsed time; the reference arm runs on
-rank 0 only."""
+bench.py runs one process per GPU.  By default there is no data-path
+collective (each rank searches its own resident copy: weak scaling); the only
+communication is a barrier and the max-reduction of the elapsed time, and the
+reference arm runs on rank 0 only.  With --shard each rank searches its shard
+of one database and the score slices are all-gathered inside the end-to-end
+step; here the CPU oracle stands in for each rank's GPU search."""
 
 import json
 import os
@@ -62,3 +64,43 @@ def test_two_gloo_ranks(tmp_path):
     assert line["impl"] == "reference" and line["unit"] == "GCUPS" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle"
     assert r1["stdout"] == ""
+
+
+def _shard_worker(rank, world, port, outdir):
+    import sys
+
+    import numpy as np
+    import torch.distributed as dist
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    import oracle
+    from paper_2412_08308_gb300.shard import partition
+    from workload import make_workload
+    from workload.matrices import BLOSUM62
+
+    w = make_workload("one_query_vs_2k", n_db=150)
+    parts = partition(w["db"].lengths, world)
+    shard = w["db"].subset(parts[rank])
+    full = bench.sharded_e2e_step(lambda: oracle.scores(w["queries"], shard, BLOSUM62, 10, 2), parts, dist)
+    np.save(os.path.join(outdir, f"sharded{rank}.npy"), full)
+    dist.destroy_process_group()
+
+
+def test_sharded_bench_step_gathers_in_caller_order(tmp_path):
+    import numpy as np
+
+    import oracle
+    from workload import make_workload
+    from workload.matrices import BLOSUM62
+
+    oracle.build()
+    mp.start_processes(_shard_worker, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True,
+                       start_method="spawn")
+    w = make_workload("one_query_vs_2k", n_db=150)
+    exp = oracle.scores(w["queries"], w["db"], BLOSUM62, 10, 2)
+    for r in range(2):
+        assert np.array_equal(np.load(tmp_path / f"sharded{r}.npy"), exp)
