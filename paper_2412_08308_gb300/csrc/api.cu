@@ -51,6 +51,11 @@ int cuda_fail(cudaError_t e, const char *what) {
 
 inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
+// transposed jobs: rows per lane, and each lane's rows as two half-chains a
+// column apart or not
+constexpr int kTrackRows = 16;
+constexpr bool kTrackSplit = false;
+
 
 int sm_count(int dev) {
   int n = 0;
@@ -143,6 +148,16 @@ struct sw_queries {
   // other queries against the long units
   int64_t n_bjobs = 0, n_bands = 0, n_btargets = 0, band_ring_bytes = 0;
   int bgrid = 1, bR = 8;
+  // transposed jobs (small batches): database row tracks against each short query
+  int64_t n_tjobs = 0, n_tbands = 0, n_tlanes = 0, track_ring_bytes = 0, qt_bytes = 16;
+  int tgrid = 1, tR = 16;
+  TrackJob *d_tjobs = nullptr;
+  int32_t *d_tjob_of = nullptr;
+  TrackLane *d_tlanes = nullptr;
+  uint8_t *d_qt = nullptr;
+  int64_t *d_qt_off = nullptr;
+  int32_t *d_qt_npad = nullptr;
+  unsigned long long *d_trings = nullptr;
   BandJob *d_bjobs = nullptr;
   int32_t *d_bjob_of = nullptr;
   int2 *d_btpos = nullptr;
@@ -155,6 +170,7 @@ struct sw_queries {
   int32_t *gscores = nullptr;
   // word layout: [0] inter counter, [1] inter rescue counter, [2] status, [3] inter rescue tasks,
   // [4] intra (packed) counter, [5] intra (int32) counter, [6] query-pair counter, [7] band counter,
+  // (the transposed jobs' counter is word [1], the inter rescue counter, unused in small batches)
   // [8, 8+nq) inter flag counts, [8+nq, 8+2nq) intra flag counts   -- zeroed every search
   // [8+2nq] inter tasks, [9+2nq] intra packed tasks, [10+2nq] intra int32 tasks,
   // [11+2nq] query-pair tasks -- constants
@@ -453,31 +469,50 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
     return packed && (int64_t)sc.maxp * std::min<int64_t>(qlen(q), n_upper) > sc.thresh;
   };
 
-  // --- band-stream jobs (k_band.cu).  In a batch too small to fill the GPU,
-  // a query of at least two bands (512 rows) runs against every database
-  // unit, and a shorter query against the long units, as pipelines of
-  // 256-row bands, one warp each: a job is one query and a stream of units,
-  // all its bands sweeping the stream together.  A unit whose pair with the
-  // query could pass the 16-bit range is split into its sequences in int32;
-  // the others keep two sequences per 32-bit word.  Streams are cut so that
-  // every warp of one launch gets about the same number of columns (the
-  // longest unit at least), and their rings (one entry per stream column
-  // between consecutive bands) must fit a memory budget; otherwise the
-  // batch takes the regular plan.
-  std::vector<char> band_q(n_queries, 0);
+  // --- small batches: band-stream jobs and transposed jobs (k_band.cu).  In
+  // a batch too small to fill the GPU, the longest chains of the inter-task
+  // kernel set the time while most SMs idle, so:
+  //  - a query of at least two bands (512 rows) runs against every database
+  //    unit as pipelines of 256-row bands, one warp each: a job is one query
+  //    and a stream of units, all its bands sweeping the stream together.  A
+  //    unit whose pair with the query could pass the 16-bit range is split
+  //    into its sequences in int32; the others keep two sequences per word.
+  //    Streams are cut so that every warp of one launch gets about the same
+  //    number of columns (the longest unit at least);
+  //  - every shorter query runs transposed: the database sequences are the
+  //    rows, stacked in row tracks of whole 8-row lanes, and the query the
+  //    columns; each band of a track is one warp, several short sequences
+  //    share a band, and the bands of a longer one run as a pipeline.  In
+  //    packed mode two tracks share each word (one query residue per column:
+  //    query-pair words), except sequences whose pair with the longest of
+  //    these queries could pass the 16-bit range (int32 tracks).
+  // The inter- and intra-task kernels are then not used.  If the rings (one
+  // entry per column between consecutive bands) do not fit a memory budget,
+  // the batch takes the regular plan.
+  std::vector<char> band_q(n_queries, 0), track_q(n_queries, 0), small_q(n_queries, 0);
   std::vector<BandJob> bjobs;
   std::vector<int32_t> bjob_of;
   std::vector<int2> btpos;
+  std::vector<TrackJob> tjobs;
+  std::vector<int32_t> tjob_of;
+  std::vector<TrackLane> tlanes;
+  std::vector<int64_t> qt_off(std::max<int64_t>(n_queries, 1), 0);
+  std::vector<int32_t> qt_npad(std::max<int64_t>(n_queries, 1), 16);
   bool band_mode = false;
   if (o.band_stream != 1 && (o.band_stream == 2 || latency_bound) && n > 0 && n_queries > 0) {
     const int brows = 32 * bR;
-    bool any = n_long > 0;
+    bool any_band = false, any_track = false;
     for (int64_t q = 0; q < n_queries; ++q) {
       band_q[q] = qlen(q) >= 2 * brows;
-      any |= band_q[q] != 0;
+      track_q[q] = !band_q[q];
+      any_band |= band_q[q] != 0;
+      any_track |= track_q[q] != 0;
     }
-    const int bocc = any ? band_max_ctas_per_sm(bR) : 0;
-    if (any && bocc > 0) {
+    const int bocc = any_band ? band_max_ctas_per_sm(bR) : 1;
+    const int tocc = any_track ? track_max_ctas_per_sm(kTrackRows, kTrackSplit) : 1;
+    int64_t ring = 0, band = 0, tring = 0, tband = 0;
+    if (bocc > 0 && tocc > 0) {
+      // band jobs: each band query against every unit
       struct BList {
         int32_t q, packed, nb;
         std::vector<int2> t;
@@ -487,11 +522,10 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
       std::vector<BList> lists;
       double total = 0;
       for (int64_t q = 0; q < n_queries; ++q) {
-        const int64_t u1 = band_q[q] ? Q->n_units : n_long;
-        if (u1 == 0) continue;
+        if (!band_q[q]) continue;
         const int32_t nb = std::max(1, (qlen(q) + brows - 1) / brows);
         BList lp{(int32_t)q, 1, nb, {}, {}, 0}, li{(int32_t)q, 0, nb, {}, {}, 0};
-        for (int64_t u = 0; u < u1; ++u) {
+        for (int64_t u = 0; u < Q->n_units; ++u) {
           const int32_t a = unit_seq(packed ? 2 * u : u), b = packed ? unit_seq(2 * u + 1) : a;
           if (packed && !may_flag(q, unit_len(u))) {
             lp.t.push_back(make_int2(a, b));
@@ -539,7 +573,6 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
       std::stable_sort(bjobs.begin(), bjobs.end(), [](const BandJob &x, const BandJob &y) {
         return (int64_t)x.nb * x.cols > (int64_t)y.nb * y.cols;
       });
-      int64_t ring = 0, band = 0;
       for (size_t k = 0; k < bjobs.size(); ++k) {
         bjobs[k].band0 = (int32_t)band;
         bjobs[k].ring0 = ring;
@@ -547,8 +580,127 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
         for (int b = 0; b < bjobs[k].nb; ++b) bjob_of.push_back((int32_t)k);
         band += bjobs[k].nb;
       }
+
+      // transposed jobs: the database in row tracks, each short query as columns
+      if (any_track) {
+        const int tR = kTrackRows;
+        const int32_t kRows = 32 * tR;  // rows per band
+        int32_t mtq = 0;
+        int64_t qt = 0;
+        for (int64_t q = 0; q < n_queries; ++q) {
+          if (!track_q[q]) continue;
+          mtq = std::max(mtq, qlen(q));
+          qt_npad[q] = (int32_t)std::max<int64_t>(kColBlock, round_up(qlen(q), kColBlock));
+          qt_off[q] = qt;
+          qt += qt_npad[q];
+        }
+        Q->qt_bytes = std::max<int64_t>(qt, 16);
+        // tracks: a sequence longer than a band gets a track of its own (its
+        // bands run as a pipeline); the others, each padded to whole lanes,
+        // are packed into one-band tracks without crossing a band boundary
+        // (sorted longest first, each into the first of the last 64 open
+        // bands with room), so those bands depend on no other band.  Empty
+        // sequences score 0 without a job.
+        struct Seg {
+          int32_t pos, row0, rows;
+        };
+        std::vector<std::vector<Seg>> trk[2];  // [0] two per word (16-bit), [1] int32
+        std::vector<int32_t> fill[2];          // rows used in each track
+        for (int64_t k = 0; k < n; ++k) {
+          const int32_t len = db->h_len[k];
+          if (len == 0) continue;
+          const int f = (packed && (int64_t)sc.maxp * std::min<int32_t>(len, mtq) <= sc.thresh) ? 0 : 1;
+          const int32_t rows = (int32_t)round_up(len, tR);
+          auto &T = trk[f];
+          auto &U = fill[f];
+          if (rows > kRows) {
+            T.push_back({{(int32_t)k, 0, rows}});
+            U.push_back(rows);
+            continue;
+          }
+          size_t i = T.size();
+          for (size_t j = T.size() > 64 ? T.size() - 64 : 0; j < T.size(); ++j)
+            if (U[j] <= kRows - rows) {
+              i = j;
+              break;
+            }
+          if (i == T.size()) {
+            T.push_back({});
+            U.push_back(0);
+          }
+          T[i].push_back({(int32_t)k, U[i], rows});
+          U[i] += rows;
+        }
+        // pipelines: packed ones pair tracks of equal band counts (longest first)
+        auto bands_of = [&](const std::vector<Seg> &t) {
+          const Seg &g = t.back();
+          return (int32_t)((g.row0 + g.rows + kRows - 1) / kRows);
+        };
+        for (int f = 0; f < 2; ++f)
+          std::stable_sort(trk[f].begin(), trk[f].end(), [&](const std::vector<Seg> &x, const std::vector<Seg> &y) {
+            return bands_of(x) > bands_of(y);
+          });
+        // the lane table of a pipeline: band b, lane l covers rows b * 32R + l R .. + R - 1
+        // (rows visited in increasing order, so each track's segment cursor only advances;
+        // a bin's segments are in placement order, which is by row)
+        auto lane_of = [&](const std::vector<Seg> *t, size_t &cur, int64_t row, int32_t &pos, int32_t &r0) {
+          pos = -1;
+          r0 = 0;
+          if (!t) return;
+          while (cur < t->size() && row >= (*t)[cur].row0 + (*t)[cur].rows) ++cur;
+          if (cur < t->size() && row >= (*t)[cur].row0) {
+            pos = (*t)[cur].pos;
+            r0 = (int32_t)(row - (*t)[cur].row0);
+          }
+        };
+        struct Pipe {
+          int32_t packed, nb, lane0;
+        };
+        std::vector<Pipe> pipes;
+        for (int f = 0; f < 2; ++f) {
+          auto &T = trk[f];
+          for (auto &t : T)  // segments by row for the cursor walk
+            std::sort(t.begin(), t.end(), [](const Seg &x, const Seg &y) { return x.row0 < y.row0; });
+          const size_t step = f == 0 ? 2 : 1;
+          for (size_t i = 0; i < T.size(); i += step) {
+            const std::vector<Seg> *ta = &T[i];
+            const std::vector<Seg> *tb = (f == 0 && i + 1 < T.size()) ? &T[i + 1] : nullptr;
+            const int32_t nb = std::max(bands_of(*ta), tb ? bands_of(*tb) : 1);
+            Pipe pp{f == 0 ? 1 : 0, nb, (int32_t)tlanes.size()};
+            size_t ca = 0, cb = 0;
+            for (int32_t b = 0; b < nb; ++b)
+              for (int l = 0; l < 32; ++l) {
+                TrackLane L{};
+                const int64_t row = (int64_t)b * kRows + (int64_t)l * tR;
+                lane_of(ta, ca, row, L.pa, L.ra);
+                lane_of(tb, cb, row, L.pb, L.rb);
+                tlanes.push_back(L);
+              }
+            pipes.push_back(pp);
+          }
+        }
+        // deeper pipelines first
+        std::stable_sort(pipes.begin(), pipes.end(), [](const Pipe &x, const Pipe &y) { return x.nb > y.nb; });
+        for (const Pipe &pp : pipes)
+          for (int64_t q = 0; q < n_queries; ++q) {
+            if (!track_q[q]) continue;
+            TrackJob j{};
+            j.q = (int32_t)q;
+            j.packed = pp.packed;
+            j.nb = pp.nb;
+            j.band0 = (int32_t)tband;
+            j.lane0 = pp.lane0;
+            j.ring0 = tring;
+            tring += (int64_t)(pp.nb - 1) * qt_npad[q];
+            for (int32_t b = 0; b < pp.nb; ++b) tjob_of.push_back((int32_t)tjobs.size());
+            tband += pp.nb;
+            tjobs.push_back(j);
+          }
+        Q->tR = tR;
+      }
       const int64_t kBandRingBudget = (int64_t)4 << 30;
-      band_mode = 8 * ring <= kBandRingBudget && band < ((int64_t)1 << 30);
+      band_mode = 8 * (ring + tring) <= kBandRingBudget && band + tband < ((int64_t)1 << 30) &&
+                  (int64_t)tlanes.size() < ((int64_t)1 << 31);
       if (band_mode) {
         Q->n_bjobs = (int64_t)bjobs.size();
         Q->n_bands = band;
@@ -557,9 +709,25 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
         Q->bR = bR;
         Q->bgrid = (int)std::max<int64_t>(1, std::min<int64_t>((band + band_threads() / 32 - 1) / (band_threads() / 32),
                                                                (int64_t)sms * bocc));
+        Q->n_tjobs = (int64_t)tjobs.size();
+        Q->n_tbands = tband;
+        Q->n_tlanes = (int64_t)tlanes.size();
+        Q->track_ring_bytes = 8 * tring;
+        Q->tgrid = (int)std::max<int64_t>(1, std::min<int64_t>((tband + track_threads() / 32 - 1) / (track_threads() / 32),
+                                                               (int64_t)sms * tocc));
+        for (int64_t q = 0; q < n_queries; ++q) small_q[q] = band_q[q] || track_q[q];
       }
     }
-    if (!band_mode) std::fill(band_q.begin(), band_q.end(), 0);
+    if (!band_mode) {
+      std::fill(band_q.begin(), band_q.end(), 0);
+      std::fill(track_q.begin(), track_q.end(), 0);
+      bjobs.clear();
+      bjob_of.clear();
+      btpos.clear();
+      tjobs.clear();
+      tjob_of.clear();
+      tlanes.clear();
+    }
   }
 
   // --- query tracks (packed mode).  Two queries share one chain, one per
@@ -576,7 +744,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   std::vector<int32_t> in_track(n_queries, 0), elig;
   if (packed && o.query_pairs == 0 && n_queries >= 2 && Q->n_single > 0) {
     for (int64_t q = 0; q < n_queries; ++q)
-      if (!may_flag(q, max_short) && !band_q[q]) elig.push_back((int32_t)q);
+      if (!may_flag(q, max_short) && !small_q[q]) elig.push_back((int32_t)q);
     if (elig.size() < 2) elig.clear();
   }
   for (int32_t q : elig) in_track[q] = 1;
@@ -696,8 +864,8 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
       plan_L = LA;
     }
   }
-  Q->n_solo = 0;
-  for (int64_t q = 0; q < n_queries; ++q) Q->n_solo += in_track[q] ? 0 : 1;
+  Q->n_solo = 0;  // queries with a profile of their own (not in query-pair tracks, not band-stream jobs)
+  for (int64_t q = 0; q < n_queries; ++q) Q->n_solo += (in_track[q] || small_q[q]) ? 0 : 1;
   Q->npairs = (int64_t)plan_L.size();  // track plans
 
   // --- per-query plans and profile layout (queries in a pair get no solo profile)
@@ -714,7 +882,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
     const int LR = d.L * R;
     d.nchunks = std::max(1, (d.m + LR - 1) / LR);
     d.chunk_stride = (int32_t)round_up((int64_t)profile_slots(d.L) * R, 128);
-    d.chunk_bytes = (in_track[q] || band_q[q]) ? 0 : kProfRows * d.chunk_stride;
+    d.chunk_bytes = (in_track[q] || small_q[q]) ? 0 : kProfRows * d.chunk_stride;
     d.prof_off = prof;
     d.qoff = q_offsets[q];
     prof += (int64_t)d.nchunks * d.chunk_bytes;
@@ -811,7 +979,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
     }
   }
   for (int64_t q = 0; q < n_queries && Q->n_units > n_long; ++q) {
-    if (in_track[q] || band_q[q]) continue;
+    if (in_track[q] || small_q[q]) continue;
     const QDesc &d = Q->qd[q];
     const int chains = warps * (32 / d.L);
     for (int64_t u0 = n_long; u0 < Q->n_units; u0 += chains) {
@@ -918,7 +1086,15 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   const size_t b_bjobof = round_up(4 * std::max<int64_t>(Q->n_bands, 1), 256);
   const size_t b_btpos = round_up((int64_t)sizeof(int2) * std::max<int64_t>(Q->n_btargets, 1), 256);
   const size_t b_brings = Q->n_bjobs ? round_up(std::max<int64_t>(Q->band_ring_bytes, 8), 256) : 0;
-  Q->bytes = b_qres + b_sub + 2 * b_qd + b_tasks + b_itasks + b_itasks32 + b_ipos32 + b_rtasks + b_prof +
+  const bool tmode = Q->n_tjobs > 0;
+  const size_t b_tjobs = tmode ? round_up((int64_t)sizeof(TrackJob) * Q->n_tjobs, 256) : 0;
+  const size_t b_tjobof = tmode ? round_up(4 * Q->n_tbands, 256) : 0;
+  const size_t b_tlanes = tmode ? round_up((int64_t)sizeof(TrackLane) * Q->n_tlanes, 256) : 0;
+  const size_t b_qt = tmode ? round_up(Q->qt_bytes, 256) : 0;
+  const size_t b_qtoff = tmode ? round_up(8 * nqm, 256) : 0;
+  const size_t b_qtnpad = tmode ? round_up(4 * nqm, 256) : 0;
+  const size_t b_trings = tmode ? round_up(std::max<int64_t>(Q->track_ring_bytes, 8), 256) : 0;
+  Q->bytes = b_tjobs + b_tjobof + b_tlanes + b_qt + b_qtoff + b_qtnpad + b_trings + b_qres + b_sub + 2 * b_qd + b_tasks + b_itasks + b_itasks32 + b_ipos32 + b_rtasks + b_prof +
              b_gbuf + b_igbuf + b_words + b_flag + b_iflag + b_qdp + b_ptasks + b_track + b_bjobs + b_bjobof +
              b_btpos + b_brings;
   cudaError_t e = cudaMallocAsync(&Q->block, Q->bytes, s);
@@ -954,6 +1130,15 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   Q->d_bjob_of = (int32_t *)take(b_bjobof);
   Q->d_btpos = (int2 *)take(b_btpos);
   Q->d_brings = Q->n_bjobs ? (unsigned long long *)take(b_brings) : nullptr;
+  if (tmode) {
+    Q->d_tjobs = (TrackJob *)take(b_tjobs);
+    Q->d_tjob_of = (int32_t *)take(b_tjobof);
+    Q->d_tlanes = (TrackLane *)take(b_tlanes);
+    Q->d_qt = take(b_qt);
+    Q->d_qt_off = (int64_t *)take(b_qtoff);
+    Q->d_qt_npad = (int32_t *)take(b_qtnpad);
+    Q->d_trings = (unsigned long long *)take(b_trings);
+  }
   Q->d_upos = const_cast<int32_t *>(db->d_ident) + s0;  // the short sequences, in sorted order
   Q->n_upos = n + 1 - s0;
 
@@ -968,7 +1153,8 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
                  (int64_t)sizeof(QDesc) * Q->npairs + (int64_t)sizeof(TrackChunk) * (int64_t)Q->track.size() +
                  (int64_t)sizeof(Task) * (Q->n_tasks + Q->n_itasks + Q->n_itasks32 + Q->n_ptasks) +
                  4 * (int64_t)ipos32.size() + 16 + (int64_t)sizeof(BandJob) * Q->n_bjobs + 4 * Q->n_bands +
-                 (int64_t)sizeof(int2) * Q->n_btargets;
+                 (int64_t)sizeof(int2) * Q->n_btargets + (int64_t)sizeof(TrackJob) * Q->n_tjobs + 4 * Q->n_tbands +
+                 (int64_t)sizeof(TrackLane) * Q->n_tlanes + (tmode ? Q->qt_bytes + 12 * n_queries : 0);
   e = cudaSuccess;
   if (q_offsets[n_queries] > 0)
     e = cudaMemcpyAsync(Q->d_qres, queries, q_offsets[n_queries], cudaMemcpyHostToDevice, s);
@@ -1000,6 +1186,20 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
       e = cudaMemcpyAsync(Q->d_bjob_of, bjob_of.data(), 4 * Q->n_bands, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(Q->d_btpos, btpos.data(), sizeof(int2) * Q->n_btargets, cudaMemcpyHostToDevice, s);
+  }
+  std::vector<uint8_t> qtbuf;
+  if (e == cudaSuccess && tmode) {
+    qtbuf.assign((size_t)Q->qt_bytes, (uint8_t)kPadCode);
+    for (int64_t q = 0; q < n_queries; ++q)
+      if (track_q[q] && qlen(q) > 0) memcpy(&qtbuf[qt_off[q]], queries + q_offsets[q], (size_t)qlen(q));
+    e = cudaMemcpyAsync(Q->d_tjobs, tjobs.data(), sizeof(TrackJob) * Q->n_tjobs, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(Q->d_tjob_of, tjob_of.data(), 4 * Q->n_tbands, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(Q->d_tlanes, tlanes.data(), sizeof(TrackLane) * Q->n_tlanes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Q->d_qt, qtbuf.data(), qtbuf.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Q->d_qt_off, qt_off.data(), 8 * n_queries, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Q->d_qt_npad, qt_npad.data(), 4 * n_queries, cudaMemcpyHostToDevice, s);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(Q->d_words, 0, b_words, s);
   if (e == cudaSuccess)
@@ -1048,14 +1248,15 @@ int sw_search_prepared(const sw_db *db, const sw_queries *Q, int32_t *scores_dev
     SW_CUDA(launch_build_track_profiles(Q->d_qres, Q->d_qd, Q->d_qdp, Q->d_track, (int32_t)Q->track.size(),
                                         Q->d_submat, Q->sc.pad, Q->d_prof, s),
             "track profile kernel");
-  if (Q->n_long)
+  if (Q->n_itasks || Q->n_itasks32)
     SW_CUDA(launch_build_profiles(Q->d_qres, Q->d_qdi, nq, Q->d_submat, Q->sc.pad, Q->d_prof, s),
             "profile kernel");
 
   stage.reset(new StageRange("swgb: dynamic programming"));
-  // band-stream jobs add their scores with atomicMax: every score starts at 0
-  if (Q->n_bjobs) SW_CUDA(cudaMemsetAsync(scores_dev, 0, 4 * (size_t)Q->nq * (size_t)db->n, s), "memset");
-  const bool band_timing = Q->timing && Q->n_bjobs;
+  // band-stream and transposed jobs add their scores with atomicMax: every score starts at 0
+  const bool small = Q->n_bjobs || Q->n_tjobs;
+  if (small) SW_CUDA(cudaMemsetAsync(scores_dev, 0, 4 * (size_t)Q->nq * (size_t)db->n, s), "memset");
+  const bool band_timing = Q->timing && small;
   if (band_timing) SW_CUDA(cudaEventRecord(Q->ev0, s), "event");
 
   InterArgs a{};
@@ -1132,6 +1333,30 @@ int sw_search_prepared(const sw_db *db, const sw_queries *Q, int32_t *scores_dev
     SW_CUDA(cudaEventRecord(Q->join, Q->side), "event");
   }
 
+  if (Q->n_tjobs) {  // transposed jobs, on the caller's stream beside the band-stream ones
+    SW_CUDA(cudaMemsetAsync(Q->d_trings, 0, (size_t)Q->track_ring_bytes, s), "memset");
+    TrackArgs ta{};
+    ta.db = db->view;
+    ta.lanes = Q->d_tlanes;
+    ta.jobs = Q->d_tjobs;
+    ta.band_job = Q->d_tjob_of;
+    ta.nbands = (int32_t)Q->n_tbands;
+    ta.band_counter = w + 1;
+    ta.qt = Q->d_qt;
+    ta.qt_off = Q->d_qt_off;
+    ta.qt_npad = Q->d_qt_npad;
+    ta.submat = Q->d_submat;
+    ta.rings = Q->d_trings;
+    ta.out = scores_dev;
+    ta.out_stride = db->n;
+    ta.sc = Q->sc;
+    ta.status = w + 2;
+    ta.n_lanes = Q->n_tlanes;
+    ta.ring_entries = Q->track_ring_bytes / 8;
+    ta.out_size = Q->nq * db->n;
+    ta.qt_bytes = Q->qt_bytes;
+    SW_CUDA(launch_track(ta, Q->tR, kTrackSplit, Q->tgrid, s), "band-stream kernel (transposed jobs)");
+  }
   if (Q->timing && !band_timing && (Q->n_tasks || Q->n_ptasks)) SW_CUDA(cudaEventRecord(Q->ev0, s), "event");
   if (Q->n_ptasks) {  // query pairs, one short database sequence per chain
     InterArgs p = a;
@@ -1279,11 +1504,12 @@ int sw_queries_info(const sw_queries *q, int64_t *h2d_bytes, int64_t *device_byt
   if (launches) {
     int64_t k = 0;
     if (q->nq > 0 && q->db->n > 0) {
-      k = (q->n_solo ? 1 : 0) + (q->npairs ? 1 : 0) + (q->n_long ? 1 : 0);  // profile builds
+      k = (q->n_solo ? 1 : 0) + (q->npairs ? 1 : 0) + ((q->n_itasks || q->n_itasks32) ? 1 : 0);  // profile builds
       k += (q->n_tasks ? 1 : 0) + (q->n_ptasks ? 1 : 0);  // inter-task kernels
       k += (q->n_tasks && q->inter_may_flag) ? 2 : 0;     // rescue tasks + int32 rescue
       k += (q->n_itasks ? 1 : 0) + (q->n_itasks32 ? 1 : 0);
       k += q->n_bjobs ? 1 : 0;  // band-stream kernel
+      k += q->n_tjobs ? 1 : 0;  // transposed jobs
     }
     *launches = k;
   }

@@ -179,6 +179,32 @@ __device__ __forceinline__ void word_rows(uint32_t hd0, const uint32_t (&p)[N], 
   }
 }
 
+// word_rows with a one-operation chain down the rows, for kernels bound by
+// one chain's latency rather than by throughput (the band-stream and
+// transposed jobs of small batches).  U = max(H_diag + SM, E, 0) does not
+// depend on the row above; since Ge <= Go, the F passed down is
+// max(F - Ge, H - Go) = max(F - Ge, U - Go, F - Go) = max(F - Ge, U - Go), so
+// the only operation on the chain is that max-add, and H = max(U, F), the
+// running best and E' = max(E - Ge, H - Go) hang off it.  Same five maxima
+// per word as word_rows, one more addition (U - Go beside H - Go).
+template <int R0, int N, int R>
+__device__ __forceinline__ void word_rows_short(uint32_t hd0, const uint32_t (&p)[N], uint32_t (&E)[R],
+                                                uint32_t (&Hl)[R], uint32_t &f, uint32_t &S, const Consts &cs) {
+  static_assert(R0 + N <= R, "rows in range");
+  uint32_t u[N];
+  u[0] = __vimax_s16x2_relu(__vadd2(hd0, p[0]), E[R0]);  // max(H_diag + SM, E, 0)
+#pragma unroll
+  for (int r = 1; r < N; ++r) u[r] = __vimax_s16x2_relu(__vadd2(Hl[R0 + r - 1], p[r]), E[R0 + r]);
+#pragma unroll
+  for (int r = 0; r < N; ++r) {
+    const uint32_t h = __vmaxs2(u[r], f);  // H = max(U, F)
+    f = __vmaxs2(__vsub2(f, cs.geW), __vsub2(u[r], cs.goW));
+    S = __vmaxs2(S, h);
+    E[R0 + r] = __vmaxs2(__vsub2(E[R0 + r], cs.geW), __vsub2(h, cs.goW));
+    Hl[R0 + r] = h;
+  }
+}
+
 template <int FORM>
 using Word = typename std::conditional<FORM != kFormInt32, uint32_t, int32_t>::type;
 
@@ -243,7 +269,8 @@ __device__ __forceinline__ void lane_reset(LaneState<R, FORM> &st, const Consts 
 // 32 lanes of a warp read 32 consecutive 16-byte groups: no bank conflict).
 // Outputs the (H, F) pair for the row below: int32 passes (H, F) of the last
 // row; packed passes (H of the last row, F of the row below it).
-template <int R, int FORM>
+// SHORTF (16-bit forms): rows by word_rows_short, the one-operation chain.
+template <int R, int FORM, bool SHORTF = false>
 __device__ __forceinline__ void column_step(LaneState<R, FORM> &st, const uint8_t *prow, int stride,
                                             uint32_t res, Word<FORM> inH, Word<FORM> inF, const Consts &cs,
                                             Word<FORM> &S, Word<FORM> &outH, Word<FORM> &outF, int gstride = 0) {
@@ -257,7 +284,8 @@ __device__ __forceinline__ void column_step(LaneState<R, FORM> &st, const uint8_
       pw[4 * i + 0] = v.x; pw[4 * i + 1] = v.y; pw[4 * i + 2] = v.z; pw[4 * i + 3] = v.w;
     }
     uint32_t f = (uint32_t)inF, s = (uint32_t)S;
-    word_rows<0, R>((uint32_t)st.hdiag, pw, st.E, st.Hl, f, s, cs);
+    if constexpr (SHORTF) word_rows_short<0, R>((uint32_t)st.hdiag, pw, st.E, st.Hl, f, s, cs);
+    else word_rows<0, R>((uint32_t)st.hdiag, pw, st.E, st.Hl, f, s, cs);
     S = (W)s;
     outH = st.Hl[R - 1];
     outF = (W)f;
@@ -269,7 +297,8 @@ __device__ __forceinline__ void column_step(LaneState<R, FORM> &st, const uint8_
 #pragma unroll
     for (int r = 0; r < R; ++r) pw[r] = prmt(pa[r >> 2], pb[r >> 2], sel_pair(r & 3));  // (SM_a, SM_b), signed halves
     uint32_t f = (uint32_t)inF, s = (uint32_t)S;
-    word_rows<0, R>((uint32_t)st.hdiag, pw, st.E, st.Hl, f, s, cs);
+    if constexpr (SHORTF) word_rows_short<0, R>((uint32_t)st.hdiag, pw, st.E, st.Hl, f, s, cs);
+    else word_rows<0, R>((uint32_t)st.hdiag, pw, st.E, st.Hl, f, s, cs);
     S = (W)s;
     outH = st.Hl[R - 1];
     outF = (W)f;

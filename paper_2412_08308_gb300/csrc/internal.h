@@ -171,6 +171,52 @@ struct BandArgs {
   int64_t out_size;           // entries of `out`
   int64_t n_tpos;             // entries of `tpos`
 };
+// Transposed jobs of the band-stream kernel (k_band.cu): for the short queries
+// of a small batch the database sequences are the rows -- stacked end to end
+// in row tracks, each padded to whole lanes of R rows -- and the query is the
+// columns.  A track is cut into bands of 32 lanes x R rows, one warp each; a
+// lane whose first row starts a sequence takes the matrix top boundary instead
+// of the row above, so one band holds several short sequences, and the bands
+// of a sequence that spans several run as a pipeline, as above.
+struct TrackLane {
+  int32_t pa, ra;  // rows of the low half (int32: the only track): sorted position, first row (-1: idle lane)
+  int32_t pb, rb;  // rows of the high half (16-bit halves only)
+};
+struct TrackJob {
+  int32_t q;       // the query: the columns, and the row of scores written
+  int32_t packed;  // 1: two row tracks in the 16-bit halves; 0: one track, int32 cells
+  int32_t nb;      // bands
+  int32_t band0;   // global index of the job's band 0
+  int32_t lane0;   // band b's lanes at TrackArgs::lanes[lane0 + 32 b ...]
+  int32_t pad_;
+  int64_t ring0;   // entry offset of ring 0 (between bands 0 and 1); rings are qt_npad[q] long
+};
+struct TrackArgs {
+  DbView db;                  // the rows' sequences
+  const TrackLane *lanes;
+  const TrackJob *jobs;
+  const int32_t *band_job;    // [nbands] job of each global band
+  int32_t nbands;
+  int32_t *band_counter;      // zeroed before the launch
+  const uint8_t *qt;          // queries padded to multiples of 16 with the pad code
+  const int64_t *qt_off;      // [nq] offset of each padded query in qt
+  const int32_t *qt_npad;     // [nq] padded length
+  const int8_t *submat;       // 20x20 (row = query residue)
+  unsigned long long *rings;  // zeroed before the launch
+  int32_t *out;               // [nq][out_stride] caller order, the jobs' rows zeroed before (atomicMax)
+  int64_t out_stride;
+  Scoring sc;
+  int32_t *status;
+  // buffer sizes, tested by the checked build (-DSW_CHECK) before every access
+  int64_t n_lanes, ring_entries, out_size, qt_bytes;
+};
+// R: rows per lane of the transposed jobs (8 or 16: bands of 256 or 512 database rows);
+// split: each lane's rows as two half-chains a column apart (see column_step_split)
+bool track_supported_R(int R);
+int track_max_ctas_per_sm(int R, bool split);  // plan time: raises the shared-memory limit; 0 on failure
+int track_threads();
+cudaError_t launch_track(const TrackArgs &a, int R, bool split, int grid, cudaStream_t s);
+
 int band_threads();
 bool band_supported_R(int R);  // rows per lane: 8 or 16 (bands of 256 or 512 query rows)
 size_t band_smem_bytes(int R);
