@@ -29,6 +29,7 @@ class Request:
     arrival: float
     future: Future
     admitted: float = 0.0
+    planned: float = 0.0
     done: float = 0.0
 
 
@@ -152,6 +153,9 @@ class Server:
         with torch.cuda.stream(stream):
             pq = PreparedQueries(self.db, residues, offsets, self.submat, self.gap_open, self.gap_extend,
                                  self.mode, opts=self.opts, stream=stream)
+            planned = time.perf_counter()
+            for r in take:
+                r.planned = planned
             out_dev = torch.empty((len(take), self.db.n), dtype=torch.int32, device="cuda")
             out_host = torch.empty((len(take), self.db.n), dtype=torch.int32, pin_memory=True)
             pq.search(out_dev, stream=stream)
@@ -210,5 +214,13 @@ class Server:
         lat = np.array([r.done - r.arrival for r in self.completed])
         if lat.size == 0:
             return {}
-        return {"requests": int(lat.size), "p50_ms": float(np.percentile(lat, 50) * 1e3),
-                "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3)}
+        queue = np.array([r.admitted - r.arrival for r in self.completed])
+        plan = np.array([r.planned - r.admitted for r in self.completed])
+        p50 = float(np.percentile(lat, 50) * 1e3)
+        # a request's latency = waiting for admission + planning its batch
+        # (sw_queries_prepare, on the dispatcher thread) + its batch's search
+        return {"requests": int(lat.size), "p50_ms": p50, "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "mean_ms": float(lat.mean() * 1e3), "queue_ms_p50": float(np.median(queue) * 1e3),
+                "plan_ms_p50": float(np.median(plan) * 1e3), "plan_ms_mean": float(plan.mean() * 1e3),
+                "plan_share_of_p50": float(np.median(plan) * 1e3 / p50) if p50 > 0 else 0.0,
+                "plan_share_of_mean": float(plan.mean() / lat.mean()) if lat.mean() > 0 else 0.0}

@@ -56,6 +56,7 @@ def test_results_same_alone_and_in_the_mix(api, mode):
         np.testing.assert_array_equal(got[i], exp[i])
     st = srv.latency_stats()
     assert st["requests"] == len(qs) and st["p99_ms"] >= st["p50_ms"] > 0
+    assert 0 < st["plan_ms_p50"] < st["p50_ms"] and 0 < st["plan_share_of_p50"] < 1
     db.close()
 
 
