@@ -108,15 +108,16 @@ typedef struct sw_options {
                               into the two 16-bit halves where no lane can overflow (one
                               database sequence per chain), 1 = never pair (two database
                               sequences per chain for every query) */
-  int32_t band_stream;     /* batches too small to fill the GPU (0 = auto): queries of at least
-                              two bands against every database unit, and the shorter queries
-                              against the units of at least `cutover` residues, run in the
-                              band-stream kernel -- a query's rows cut into bands (see
-                              band_rows), one warp each, all bands of a query running as a
-                              pipeline over a stream of units (the intra-task kernel is not
-                              used); 1 = never; 2 = for every batch, however large */
+  int32_t band_stream;     /* batches too small to fill the GPU (0 = auto) run in the band-stream
+                              kernel instead of the inter- and intra-task kernels: a query of at
+                              least two bands (see band_rows) against every database unit, its
+                              rows cut into bands, one warp each, the bands of a query running
+                              as a pipeline over a stream of units; every shorter query
+                              transposed, the database sequences stacked as rows in bands of
+                              512 rows and the query's residues as the columns; 1 = never;
+                              2 = for every batch, however large */
   int32_t band_rows;       /* query rows per lane of the band-stream kernel: 8 or 16 (bands of
-                              256 or 512 rows); 0 = 8 */
+                              256 or 512 rows); 0 = 16 */
   int32_t reserved[1];     /* must be 0 */
 } sw_options;
 

@@ -75,7 +75,7 @@ def options(cutover=0, rows_per_lane=0, lanes_per_chain=0, intra_rows=0, query_p
     """Tuning knobs of a query batch (sw_options); 0 keeps the default.
     query_pairs=False keeps every packed query in the two-sequences-per-chain form;
     band_stream: "auto" (batches too small to fill the GPU), "never" or "always";
-    band_rows: rows per lane of the band-stream kernel (8 or 16)."""
+    band_rows: rows per lane of the band-stream kernel (8 or 16; 0 = 16)."""
     return N.SwOptions(int(cutover), int(rows_per_lane), int(lanes_per_chain), int(intra_rows),
                        0 if query_pairs else 1, BAND_STREAM[band_stream], int(band_rows))
 

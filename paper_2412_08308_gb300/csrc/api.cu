@@ -351,7 +351,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   sw_options o{};
   if (opts) o = *opts;
   if (o.reserved[0]) return fail(SW_EINVAL, "sw_queries_prepare: reserved option fields must be 0");
-  const int bR = o.band_rows ? o.band_rows : 8;
+  const int bR = o.band_rows ? o.band_rows : 16;
   if (!band_supported_R(bR)) return fail(SW_EINVAL, "sw_queries_prepare: band_rows must be 8 or 16");
   if (o.band_stream < 0 || o.band_stream > 2) return fail(SW_EINVAL, "sw_queries_prepare: band_stream must be 0, 1 or 2");
   if (o.query_pairs != 0 && o.query_pairs != 1) return fail(SW_EINVAL, "sw_queries_prepare: query_pairs must be 0 or 1");
@@ -508,7 +508,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
       any_band |= band_q[q] != 0;
       any_track |= track_q[q] != 0;
     }
-    const int bocc = any_band ? band_max_ctas_per_sm(bR) : 1;
+    int bocc = any_band ? band_max_ctas_per_sm(bR) : 1;
     const int tocc = any_track ? track_max_ctas_per_sm(kTrackRows, kTrackSplit) : 1;
     int64_t ring = 0, band = 0, tring = 0, tband = 0;
     if (bocc > 0 && tocc > 0) {
@@ -517,7 +517,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
         int32_t q, packed, nb;
         std::vector<int2> t;
         std::vector<int32_t> w;  // columns of each unit
-        int64_t cols = 0;
+        int64_t cols = 0, widest = 0;
       };
       std::vector<BList> lists;
       double total = 0;
@@ -545,17 +545,40 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
         for (BList *L : {&lp, &li})
           if (!L->t.empty()) {
             total += (double)L->nb * (double)L->cols;
+            for (int32_t x : L->w) L->widest = std::max<int64_t>(L->widest, x);
             lists.push_back(std::move(*L));
           }
       }
-      const double wbudget = (double)sms * bocc * (band_threads() / 32);
-      const int64_t per_warp = std::max<int64_t>(1, (int64_t)std::ceil(total / wbudget));
+      // Streams are cut into jobs of about per_warp columns, two jobs per warp
+      // of the launch (a warp that finishes early takes a band of the second
+      // wave, whose pipeline fill overlaps the first wave's drain).  Units
+      // are not cut, so an int32 unit wider than per_warp makes a job that
+      // sets the pace of the launch: it runs in bands of half the height
+      // (half the work per step; its steps run one after the other), and if
+      // its steps, slowed by the other warps that share its SM sub-partition
+      // (two per CTA per SM, all computing), would outlast the launch's
+      // average load, the launch keeps one CTA per SM instead of two.
+      constexpr double kWaves = 2.0;
+      const int wpc = band_threads() / 32;  // warps per CTA
+      auto per_warp_at = [&](int occ) {
+        return std::max<int64_t>(1, (int64_t)std::ceil(total / ((double)sms * occ * wpc * kWaves)));
+      };
+      if (bocc > 1) {
+        const int64_t pw = per_warp_at(bocc);
+        double crit = 0;  // steps of the widest oversized int32 unit, in full-height band steps
+        for (const BList &L : lists)
+          if (!L.packed && L.widest > pw) crit = std::max(crit, 0.5 * (double)L.widest);
+        const double warps_per_smsp = (double)bocc * wpc / 4.0;
+        const double load = total / ((double)sms * 4.0);  // full-height band steps per SM sub-partition
+        if (crit * warps_per_smsp > 1.3 * load) bocc = 1;
+      }
+      const int64_t per_warp = per_warp_at(bocc);
       for (const BList &L : lists) {
         size_t i = 0;
         while (i < L.t.size()) {
           BandJob j{};
           j.q = L.q;
-          j.packed = L.packed;
+          j.form = L.packed ? kBandPacked : kBandInt32;
           j.nb = L.nb;
           j.t_begin = (int32_t)btpos.size();
           int64_t cols = 0;
@@ -566,6 +589,14 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
           }
           j.t_count = (int32_t)(btpos.size() - j.t_begin);
           j.cols = cols;
+          // an int32 unit wider than the budget (a long query against a long
+          // sequence whose pair could pass the 16-bit range) makes the job
+          // that sets the pace of the launch: bands of half the height halve
+          // the work of each of its steps, which run one after the other
+          if (!L.packed && cols > per_warp) {
+            j.form = kBandInt32Half;
+            j.nb = std::max(1, (qlen(L.q) + brows / 2 - 1) / (brows / 2));
+          }
           bjobs.push_back(j);
         }
       }

@@ -140,11 +140,15 @@ cudaError_t launch_pair(const PairBandArgs &a, int R, int grid, int threads, siz
 // short query's against long database units) cut into bands of 32 lanes x R
 // rows, one warp each, all bands of a job running as a pipeline over the
 // job's stream of database units.
+// BandJob::form
+constexpr int32_t kBandInt32 = 0;      // one sequence per unit, int32 cells, bands of 32 R rows
+constexpr int32_t kBandPacked = 1;     // two sequences per unit in the 16-bit halves (pairs that
+                                       // cannot pass the 16-bit range), bands of 32 R rows
+constexpr int32_t kBandInt32Half = 2;  // int32 as kBandInt32, bands of 32 R / 2 rows
 struct BandJob {
   int32_t q;        // query: its rows are cut into the bands; its row of scores is written
-  int32_t packed;   // 1: a unit is two sequences in the 16-bit halves (pairs that cannot pass
-                    //    the 16-bit range); 0: one sequence, int32 cells
-  int32_t nb;       // bands (32 R query rows each)
+  int32_t form;     // kBandInt32, kBandPacked or kBandInt32Half
+  int32_t nb;       // bands (32 R or 32 R / 2 query rows each)
   int32_t t_begin;  // first unit in BandArgs::tpos
   int32_t t_count;  // units of the stream, in order
   int32_t band0;    // global index of the job's band 0

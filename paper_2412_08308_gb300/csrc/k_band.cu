@@ -233,6 +233,7 @@ __device__ __forceinline__ bool band_unit(const BandArgs &a, const uint8_t *__re
 
 template <int R>
 __global__ void __launch_bounds__(kBandStreamThreads, 2) band_stream_kernel(const BandArgs a) {
+  constexpr int RH = R / 2;  // rows per lane of kBandInt32Half jobs
   extern __shared__ __align__(128) uint8_t smem[];
   int8_t *sm = reinterpret_cast<int8_t *>(smem);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -250,8 +251,10 @@ __global__ void __launch_bounds__(kBandStreamThreads, 2) band_stream_kernel(cons
     const BandJob job = a.jobs[a.band_job[g]];
     const int b = g - job.band0;
     const QDesc qd = a.qd[job.q];
+    const bool half = job.form == kBandInt32Half;
     __syncwarp();
-    build_band_profile<R>(prof, sm, a.qres + qd.qoff, qd.m, b * 32 * R, lane, a.sc.pad);
+    if (half) build_band_profile<RH>(prof, sm, a.qres + qd.qoff, qd.m, b * 32 * RH, lane, a.sc.pad);
+    else build_band_profile<R>(prof, sm, a.qres + qd.qoff, qd.m, b * 32 * R, lane, a.sc.pad);
     __syncwarp();
     const unsigned long long *ring_in = b > 0 ? a.rings + job.ring0 + (int64_t)(b - 1) * job.cols : nullptr;
     unsigned long long *ring_out = b + 1 < job.nb ? a.rings + job.ring0 + (int64_t)b * job.cols : nullptr;
@@ -262,7 +265,7 @@ __global__ void __launch_bounds__(kBandStreamThreads, 2) band_stream_kernel(cons
       int2 p = make_int2(0, 0);
       if (in_range(job.t_begin + t, a.n_tpos, a.status)) p = a.tpos[job.t_begin + t];
       if (!in_range(p.x, a.db.n, a.status) || !in_range(p.y, a.db.n, a.status)) p = make_int2(0, 0);
-      if (job.packed) {
+      if (job.form == kBandPacked) {
         uint32_t S = 0u;
         ok = band_unit<R, kFormPacked>(a, prof, ring, lane, p.x, p.y, sbase, ring_in, ring_out, cs, S);
         for (int d = 16; d > 0; d >>= 1) S = __vmaxs2(S, __shfl_xor_sync(0xffffffffu, S, d));
@@ -275,7 +278,8 @@ __global__ void __launch_bounds__(kBandStreamThreads, 2) band_stream_kernel(cons
         sbase += max(a.db.npad[p.x], a.db.npad[p.y]);
       } else {
         int32_t S = 0;
-        ok = band_unit<R, kFormInt32>(a, prof, ring, lane, p.x, p.x, sbase, ring_in, ring_out, cs, S);
+        if (half) ok = band_unit<RH, kFormInt32>(a, prof, ring, lane, p.x, p.x, sbase, ring_in, ring_out, cs, S);
+        else ok = band_unit<R, kFormInt32>(a, prof, ring, lane, p.x, p.x, sbase, ring_in, ring_out, cs, S);
         for (int d = 16; d > 0; d >>= 1) S = max(S, __shfl_xor_sync(0xffffffffu, S, d));
         if (ok && lane == 0 && in_range(job.q * a.out_stride + a.db.perm[p.x], a.out_size, a.status))
           atomicMax(&orow[a.db.perm[p.x]], S);

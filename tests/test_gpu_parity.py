@@ -513,10 +513,13 @@ def test_band_stream_ragged(api, mode, band, rows):
 
 
 @pytest.mark.parametrize("mode", MODES)
-def test_band_stream_saturating_and_asymmetric(api, mode):
+@pytest.mark.parametrize("rows", [8, 16])
+def test_band_stream_saturating_and_asymmetric(api, mode, rows):
     # an asymmetric matrix with +60 matches: the band pipelines' pairs that
     # can pass 32767 (a 3,000-residue query against copies of 700 to 2,400 of
-    # its residues) run in int32, the others two sequences per word; all exact
+    # its residues) run in int32 -- the units wider than a job's share of
+    # columns in bands of half the height --, the others two sequences per
+    # word; all exact
     rng = np.random.Generator(np.random.PCG64(513))
     sm = rng.integers(-20, 6, size=(20, 20)).astype(np.int8)
     np.fill_diagonal(sm, 60)
@@ -527,7 +530,8 @@ def test_band_stream_saturating_and_asymmetric(api, mode):
     q = from_list([base, base[:600].copy(), base[2000:].copy(), rng.integers(0, 20, size=90).astype(np.uint8)])
     exp = oracle.scores(q, db, sm, 9, 3)
     assert exp.max() > 32767
-    got = _search(api, db, q, mode, sm=sm, go=9, ge=3, opts=api.options(band_stream="always", cutover=1000))
+    got = _search(api, db, q, mode, sm=sm, go=9, ge=3,
+                  opts=api.options(band_stream="always", cutover=1000, band_rows=rows))
     _assert_equal(got, exp)
 
 
