@@ -379,12 +379,13 @@ def graph_search_ms(pq, out, stream, flush, reps):
     return ts
 
 
-def small_config_block(api, name, flush, gpu, n_sm, sm_mhz, reps=50):
+def small_config_block(api, name, flush, gpu, n_sm, sm_mhz, reps=50, batch=0):
     """One of the small configurations (the 144-residue query against 2,000
     proteins; the homolog workload) in both forms: whole searches replayed
     through sw_search_graph (median of `reps`), the DP kernel's own time
     (events around it in a plain enqueue), its ALU roofline, the pairs rescued
-    and the clocks sampled during the block."""
+    and the clocks sampled during the block.  batch > 0: also `batch` seeded
+    requests of the same shape searched together, in both forms."""
     import torch
 
     from workload import WORKLOADS, make_workload
@@ -419,6 +420,28 @@ def small_config_block(api, name, flush, gpu, n_sm, sm_mhz, reps=50):
                      "roofline": roofline_of(cells / kms / 1e6, mode, n_sm, sm_mhz)}
         pq.close()
     res["packed_over_int32"] = round(res["packed"]["gcups"] / res["int32"]["gcups"], 3)
+    if batch:
+        # the same shape of request, `batch` of them in one search (the
+        # batched form): both forms, and the packed batch against the single
+        # int32 search above
+        from workload import query_batch_144
+
+        qb = query_batch_144(batch)
+        bcells = float(qb.total) * float(dbs.total)
+        outb = torch.empty((len(qb), len(dbs)), dtype=torch.int32, device="cuda")
+        bres = {"requests": batch, "queries": f"{batch} seeded queries of 144 residues", "cells": bcells}
+        for mode in ("packed", "int32"):
+            pq = api.PreparedQueries(db, qb.residues, qb.offsets, BLOSUM62, 10, 2, mode, stream=stream)
+            for _ in range(3):
+                pq.search_graph(outb, stream=stream)
+            ts = graph_search_ms(pq, outb, stream, flush, 10)
+            ms = float(np.median(ts))
+            bres[mode] = {"ms": round(ms, 4), "gcups": round(bcells / ms / 1e6, 1),
+                          "roofline": roofline_of(bcells / ms / 1e6, mode, n_sm, sm_mhz)}
+            pq.close()
+        bres["packed_over_int32"] = round(bres["packed"]["gcups"] / bres["int32"]["gcups"], 3)
+        bres["packed_batched_over_int32_single"] = round(bres["packed"]["gcups"] / res["int32"]["gcups"], 3)
+        res["batched"] = bres
     res["clocks"] = clk.stop()
     db.close()
     return res
@@ -593,7 +616,8 @@ def run_ours(args, w):
         extras["int32_roofline"] = roofline_of(cells / float(np.mean(k32)) / 1e9, "int32", n_sm, sm_mhz)
         pq32.close()
         # the other configurations of the method, each in both forms
-        extras["one_query_vs_2k"] = small_config_block(api, "one_query_vs_2k", flush, local, n_sm, sm_mhz)
+        extras["one_query_vs_2k"] = small_config_block(api, "one_query_vs_2k", flush, local, n_sm, sm_mhz,
+                                                       batch=256)
         extras["homologs_8k"] = small_config_block(api, "homologs_8k", flush, local, n_sm, sm_mhz, reps=10)
         extras["thousand_queries_vs_50k"] = batch_config_block(api, flush, n_sm, sm_mhz)
         # the paper's DNA pairwise workload at its 1M x 1M size (sw_align_pair, int32)

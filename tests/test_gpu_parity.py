@@ -59,6 +59,20 @@ def test_one_query_vs_2k_full(api, mode):
     _assert_equal(got, oracle.scores(w["queries"], w["db"], BLOSUM62, 10, 2))
 
 
+@pytest.mark.parametrize("mode", MODES)
+def test_one_query_batch_of_256(api, mode):
+    # 256 requests shaped like the single query (144 residues) searched
+    # together against the same 2,000 proteins: every query against a
+    # seeded sample of 300 of them
+    from workload import query_batch_144
+
+    w = make_workload("one_query_vs_2k")
+    q = query_batch_144(256)
+    idx = sample_indices(len(w["db"]), 300)
+    got = _search(api, w["db"], q, mode)
+    _assert_equal(got[:, idx], oracle.scores(q, w["db"].subset(idx), BLOSUM62, 10, 2))
+
+
 def _ragged(seed, n_db, n_q, qmax):
     rng = np.random.Generator(np.random.PCG64(seed))
     edge = [0, 1, 2, 15, 16, 17, 31, 32, 33, 47, 48, 49, 127, 128, 129]

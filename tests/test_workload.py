@@ -41,3 +41,11 @@ def test_mutation_model_identity():
     # roughly 90% identity along the unshifted prefix before the first indel
     same = (hom[:30] == src[:30]).mean()
     assert same > 0.6
+
+
+def test_query_batch_144():
+    from workload import query_batch_144
+
+    a, b = query_batch_144(8), query_batch_144(8)
+    assert np.array_equal(a.residues, b.residues) and a.lengths.tolist() == [144] * 8
+    assert a.residues.max() < 20 and len({bytes(a[i]) for i in range(8)}) == 8

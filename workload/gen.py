@@ -210,6 +210,14 @@ def make_workload(name, n_db=None, n_queries=None):
     return out
 
 
+def query_batch_144(n, seed=QUERY_SEED + 6):
+    """n seeded queries of 144 residues (the single query's length), drawn
+    like every other query: a batch of requests shaped like the one-query
+    workload, searched together against its 2,000 proteins."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return from_list([random_sequence(rng, 144) for _ in range(n)])
+
+
 # ---------------------------------------------------------------------------
 # DNA pairs (the paper's pairwise workload, Sec. 4.1, Table 3): the genome
 # pairs are not available; each stand-in pair is a uniform random target of
