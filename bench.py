@@ -94,6 +94,8 @@ def parse():
                     help="with N ranks: each GPU holds 1/N of the database (residue-balanced, length-stratified "
                          "shards) and searches every query against it (strong scaling); default: every GPU "
                          "searches its own full copy (weak scaling)")
+    ap.add_argument("--band-stream", default="auto", choices=["auto", "never", "always"],
+                    help="small-batch plan of the timed search (sw_options.band_stream)")
     ap.add_argument("--queries", type=int, default=0, help="use only the first K queries (profiling runs)")
     ap.add_argument("--db-limit", type=int, default=0, help="use only the first N database sequences (profiling runs)")
     return ap.parse_args()
@@ -487,7 +489,7 @@ def batch_config_block(api, flush, n_sm, sm_mhz):
     return res
 
 
-def serve_once(db, w, n_requests, stretch, mode):
+def serve_once(db, w, n_requests, stretch, mode, prestage=True):
     import threading
 
     from paper_2412_08308_gb300.serve import Server
@@ -498,7 +500,7 @@ def serve_once(db, w, n_requests, stretch, mode):
     # two queries per batch (a query pair) and two batches in flight gave the
     # lowest mean and p99 latency of the (batch, streams) settings measured;
     # shortest queries first (requests older than 1 s first of all)
-    srv = Server(db, BLOSUM62, 10, 2, mode, max_batch=2, n_streams=2, policy="sjf", age_s=1.0)
+    srv = Server(db, BLOSUM62, 10, 2, mode, max_batch=2, n_streams=2, policy="sjf", age_s=1.0, prestage=prestage)
     t0 = time.perf_counter()
     futs = []
 
@@ -524,7 +526,9 @@ def serve_once(db, w, n_requests, stretch, mode):
                "offered_gcups": round(cells / float(arrivals[-1]) / 1e9, 1),
                "sustained_gcups": round(cells / span / 1e9, 1), "wall_s": round(span, 2),
                "batching": "continuous: up to 2 queries per batch, 2 batches in flight on separate streams, "
-                           "shortest queries first (any request older than 1 s ahead)"})
+                           "shortest queries first (any request older than 1 s ahead), "
+                           + ("the next batch planned while both slots are busy" if prestage else
+                              "each batch planned when a slot frees up")})
     return st
 
 
@@ -559,7 +563,7 @@ def run_ours(args, w):
     db = api.Database.from_sequences(db_s)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    opts = api.options(query_pairs=not args.no_query_pairs)
+    opts = api.options(query_pairs=not args.no_query_pairs, band_stream=args.band_stream)
     pq = api.PreparedQueries(db, q.residues, q.offsets, BLOSUM62, 10, 2, args.mode, opts=opts)
     torch.cuda.synchronize()
     setup_ms = {"db_prepare": round(1e3 * (t1 - t0), 2), "queries_prepare": round(1e3 * (time.perf_counter() - t1), 2)}

@@ -201,7 +201,9 @@ __device__ __forceinline__ bool band_unit(const BandArgs &a, const uint8_t *__re
           inF = (W)v.y;
         }
         if constexpr (kChecked) inRes = checked_codes<FORM>(inRes, a.status);
-        column_step<R, FORM>(st, prow, 32 * R, inRes, inH, inF, cs, S, outH, outF, 0);
+        // 16-bit form in 16-row lanes: the one-operation F chain (3 % faster
+        // on the homolog workload; with 8 rows 2 % slower)
+        column_step<R, FORM, FORM == kFormPacked && R >= 16>(st, prow, 32 * R, inRes, inH, inF, cs, S, outH, outF, 0);
         outRes = inRes;
         if (tail) {
           const int j = t - LAG;

@@ -1,12 +1,14 @@
 """Continuous-batching search server over one resident database.
 
 Requests are single queries submitted at any time.  A dispatcher thread admits
-pending requests into batches as device memory and stream slots free up,
-plans each batch (sw_queries_prepare), enqueues its search
-(sw_search_prepared) and the copy of its scores to pinned host memory on one
-of several CUDA streams, and completes each request when its batch's event
-fires.  Batches on different streams run concurrently, so the work of
-requests that arrive while others are on the GPU overlaps on the device.
+pending requests into batches as device memory allows and plans each batch
+(sw_queries_prepare, on a staging stream) while every stream slot may still
+be busy, so that the next batch is planned by the time a slot frees up; it
+then enqueues the batch's search (sw_search_prepared) and the copy of its
+scores to pinned host memory on the free slot's CUDA stream, and completes
+each request when its batch's event fires.  Batches on different streams
+run concurrently, so the work of requests that arrive while others are on
+the GPU overlaps on the device.
 
 Every step of a search runs in libswgb.so; this module only schedules.
 """
@@ -52,7 +54,9 @@ class Server:
     submat      20x20 int8 scoring matrix; gap_open / gap_extend as in sw_search
     max_batch   most queries admitted into one batch
     n_streams   batches in flight at once (one CUDA stream each)
-    mem_budget  device bytes the in-flight batches may hold (scores, scratch)
+    mem_budget  device bytes the in-flight and planned batches may hold (scores, scratch)
+    prestage    plan the next batch while no slot is free (False: plan when a
+                slot frees up, on the critical path of the batch's requests)
     policy      "fifo" admits requests in arrival order; "sjf" admits the
                 shortest queries first (their cells, query length x database,
                 are the service time), except that a request waiting at least
@@ -60,7 +64,7 @@ class Server:
     """
 
     def __init__(self, db, submat, gap_open=10, gap_extend=2, mode="packed", max_batch=2, n_streams=2,
-                 mem_budget=8 << 30, opts=None, policy="sjf", age_s=1.0):
+                 mem_budget=8 << 30, opts=None, policy="sjf", age_s=1.0, prestage=True):
         import torch
 
         self.torch = torch
@@ -75,6 +79,9 @@ class Server:
         self.age_s = float(age_s)
         self.opts = opts
         self.streams = [torch.cuda.Stream() for _ in range(int(n_streams))]
+        self.stage_stream = torch.cuda.Stream()
+        self.prestage = bool(prestage)
+        self.staged = None  # (requests, PreparedQueries, bytes): planned, waiting for a slot
         self.free_slots = list(range(len(self.streams)))
         self.pending = []
         self.inflight = []
@@ -123,9 +130,13 @@ class Server:
         young = sorted((r for r in self.pending if now - r.arrival < self.age_s), key=lambda r: len(r.query))
         return aged + young
 
-    def _admit(self):
+    def _stage(self):
+        """Take the next batch from the pending requests and plan it (while
+        the slots may still be busy, if prestage; else only with a slot free)."""
         with self.lock:
-            if not self.pending or not self.free_slots:
+            if self.staged is not None or not self.pending:
+                return False
+            if not self.prestage and not self.free_slots:
                 return False
             take = []
             for r in self._order(time.perf_counter()):
@@ -139,9 +150,7 @@ class Server:
                 return False  # wait for memory to free up
             chosen = set(map(id, take))
             self.pending = [r for r in self.pending if id(r) not in chosen]
-            slot = self.free_slots.pop(0)
             self.mem_used += need
-        torch = self.torch
         now = time.perf_counter()
         for r in take:
             r.admitted = now
@@ -149,13 +158,26 @@ class Server:
         offsets = np.zeros(len(take) + 1, dtype=np.int64)
         offsets[1:] = np.cumsum(lens)
         residues = np.concatenate([r.query for r in take]) if offsets[-1] else np.zeros(0, np.uint8)
+        with self.torch.cuda.stream(self.stage_stream):
+            pq = PreparedQueries(self.db, residues, offsets, self.submat, self.gap_open, self.gap_extend,
+                                 self.mode, opts=self.opts, stream=self.stage_stream)
+        planned = time.perf_counter()
+        for r in take:
+            r.planned = planned
+        self.staged = (take, pq, need)
+        return True
+
+    def _launch(self):
+        """Enqueue the planned batch on a free slot's stream."""
+        with self.lock:
+            if self.staged is None or not self.free_slots:
+                return False
+            slot = self.free_slots.pop(0)
+        take, pq, need = self.staged
+        self.staged = None
+        torch = self.torch
         stream = self.streams[slot]
         with torch.cuda.stream(stream):
-            pq = PreparedQueries(self.db, residues, offsets, self.submat, self.gap_open, self.gap_extend,
-                                 self.mode, opts=self.opts, stream=stream)
-            planned = time.perf_counter()
-            for r in take:
-                r.planned = planned
             out_dev = torch.empty((len(take), self.db.n), dtype=torch.int32, device="cuda")
             out_host = torch.empty((len(take), self.db.n), dtype=torch.int32, pin_memory=True)
             pq.search(out_dev, stream=stream)
@@ -163,8 +185,16 @@ class Server:
             ev = torch.cuda.Event()
             ev.record(stream)
         self.inflight.append(_Batch(take, pq, out_dev, out_host, ev, slot, need))
-        self.cells += float(offsets[-1]) * float(self.db.stats()[1])
+        self.cells += float(sum(len(r.query) for r in take)) * float(self.db.stats()[1])
         return True
+
+    def _admit(self):
+        """Launch what is planned, then plan the next batch; True if either happened."""
+        launched = self._launch()
+        staged = self._stage()
+        if staged:
+            launched = self._launch() or launched
+        return launched or staged
 
     def _retire(self):
         done_any = False
@@ -195,7 +225,7 @@ class Server:
                     progressed = True
                 with self.lock:
                     finished = self.stop and not self.pending
-                if finished and not self.inflight:
+                if finished and not self.inflight and self.staged is None:
                     return
                 if not progressed:
                     self.wake.wait(timeout=0.0002)
@@ -204,6 +234,8 @@ class Server:
             self.error = e
             with self.lock:
                 waiting = self.pending + [r for b in self.inflight for r in b.requests]
+                if self.staged is not None:
+                    waiting += self.staged[0]
                 self.pending = []
             for r in waiting:
                 if not r.future.done():

@@ -29,15 +29,16 @@ def api():
     return _api
 
 
-@pytest.mark.parametrize("mode", ["packed", "int32"])
-def test_results_same_alone_and_in_the_mix(api, mode):
+@pytest.mark.parametrize("mode,prestage", [("packed", True), ("int32", True), ("packed", False)])
+def test_results_same_alone_and_in_the_mix(api, mode, prestage):
+    # prestage: the next batch is planned while every slot is busy
     from paper_2412_08308_gb300.serve import Server
 
     db_s = random_sequences(71, 3000, 300, 0.5, 20, 1000)
     qs = random_sequences(72, 40, 300, 0.5, 30, 1500)
     db = api.Database.from_sequences(db_s)
     alone = [api.search(db, qs[i], np.array([0, len(qs[i])]), BLOSUM62, 10, 2, mode)[0] for i in range(len(qs))]
-    srv = Server(db, BLOSUM62, 10, 2, mode, max_batch=6, n_streams=3)
+    srv = Server(db, BLOSUM62, 10, 2, mode, max_batch=6, n_streams=3, prestage=prestage)
     futs = []
     # bursts from two client threads, so batches overlap on the device
     def client(lo, hi):
