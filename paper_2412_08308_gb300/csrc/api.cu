@@ -1330,6 +1330,7 @@ int sw_search_prepared(const sw_db *db, const sw_queries *Q, int32_t *scores_dev
       ba.n_tpos = Q->n_btargets;
       ba.sc = Q->sc;
       ba.status = w + 2;
+      ba.short_int = packed ? 1 : 0;
       SW_CUDA(launch_band(ba, Q->bR, Q->bgrid, Q->side), "band-stream kernel");
     }
     InterArgs b = a;

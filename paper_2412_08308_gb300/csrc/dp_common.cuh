@@ -239,6 +239,39 @@ __device__ __forceinline__ void int_rows(int32_t hul, const uint32_t (&pb)[N / 4
   }
 }
 
+// int_rows with the one-operation F chain of word_rows_short, for the int32
+// units of the 16-bit path's small-batch jobs (pairs that could pass the
+// 16-bit range): the F of the row below is max(F - Ge, U - Go) with
+// U = max(H_diag + SM, E, 0), equal to Eq. 3's max(F - Ge, H - Go) because
+// H = max(U, F) and Ge <= Go; U does not depend on the row above, so the
+// chain down the rows is one subtraction and one maximum per row.  Same
+// interface and operation count as int_rows (the plain int32 form keeps
+// Algorithm 1's statement order).
+template <int R0, int N, int R>
+__device__ __forceinline__ void int_rows_short(int32_t hul, const uint32_t (&pb)[N / 4], int32_t (&E)[R],
+                                               int32_t (&Hl)[R], int32_t &hu, int32_t &fu, int32_t &S,
+                                               const Consts &cs) {
+  static_assert(R0 + N <= R && N % 4 == 0, "rows in range, whole profile words");
+  int32_t f = max(fu - cs.ge, hu - cs.go);  // the first row's F from the (H, F) above (Eq. 3)
+#pragma unroll
+  for (int r = 0; r < N; ++r) {
+    const int32_t sm = (int32_t)prmt(pb[r >> 2], 0u, sel_sext(r & 3));
+    const int32_t e = max(E[R0 + r] - cs.ge, Hl[R0 + r] - cs.go);
+    const int32_t u = max(max(hul + sm, e), 0);
+    const int32_t h = max(u, f);
+    S = max(S, h);
+    hul = Hl[R0 + r];
+    Hl[R0 + r] = h;
+    E[R0 + r] = e;
+    if (r + 1 < N) {
+      f = max(f - cs.ge, u - cs.go);
+    } else {
+      hu = h;
+      fu = f;
+    }
+  }
+}
+
 // Per-lane DP state of R rows.
 template <int R, int FORM>
 struct LaneState {
@@ -269,7 +302,7 @@ __device__ __forceinline__ void lane_reset(LaneState<R, FORM> &st, const Consts 
 // 32 lanes of a warp read 32 consecutive 16-byte groups: no bank conflict).
 // Outputs the (H, F) pair for the row below: int32 passes (H, F) of the last
 // row; packed passes (H of the last row, F of the row below it).
-// SHORTF (16-bit forms): rows by word_rows_short, the one-operation chain.
+// SHORTF: rows by word_rows_short / int_rows_short, the one-operation chain.
 template <int R, int FORM, bool SHORTF = false>
 __device__ __forceinline__ void column_step(LaneState<R, FORM> &st, const uint8_t *prow, int stride,
                                             uint32_t res, Word<FORM> inH, Word<FORM> inF, const Consts &cs,
@@ -306,7 +339,8 @@ __device__ __forceinline__ void column_step(LaneState<R, FORM> &st, const uint8_
     uint32_t pa[R / 4];
     load_prof<R>(prow + (res & 0xffu) * stride, pa);
     int32_t hu = inH, fu = inF, s = S;
-    int_rows<0, R>(st.hdiag, pa, st.E, st.Hl, hu, fu, s, cs);
+    if constexpr (SHORTF) int_rows_short<0, R>(st.hdiag, pa, st.E, st.Hl, hu, fu, s, cs);
+    else int_rows<0, R>(st.hdiag, pa, st.E, st.Hl, hu, fu, s, cs);
     S = (W)s;
     outH = (W)hu;
     outF = (W)fu;

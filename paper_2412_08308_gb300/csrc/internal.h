@@ -170,6 +170,8 @@ struct BandArgs {
   int64_t out_stride;
   Scoring sc;
   int32_t *status;            // SW_ETIMEOUT on an expired wait
+  int32_t short_int;          // 1 (16-bit batches): int32 units with the one-operation F chain;
+                              // 0 (int32 batches): Algorithm 1's statement order
   // buffer sizes, tested by the checked build (-DSW_CHECK) before every access
   int64_t ring_entries;       // entries of `rings`
   int64_t out_size;           // entries of `out`

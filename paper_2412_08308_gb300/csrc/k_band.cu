@@ -83,7 +83,7 @@ __device__ __forceinline__ void build_band_profile(uint8_t *prof, const int8_t *
 
 // One band over one database unit (columns sbase .. sbase + npad - 1 of the
 // job's stream).  Returns false when a wait expired.
-template <int R, int FORM>
+template <int R, int FORM, bool SHORTF>
 __device__ __forceinline__ bool band_unit(const BandArgs &a, const uint8_t *__restrict__ prof, uint8_t *ring,
                                           const int lane, const int posA, const int posB, const int64_t sbase,
                                           const unsigned long long *ring_in, unsigned long long *ring_out,
@@ -201,9 +201,7 @@ __device__ __forceinline__ bool band_unit(const BandArgs &a, const uint8_t *__re
           inF = (W)v.y;
         }
         if constexpr (kChecked) inRes = checked_codes<FORM>(inRes, a.status);
-        // 16-bit form in 16-row lanes: the one-operation F chain (3 % faster
-        // on the homolog workload; with 8 rows 2 % slower)
-        column_step<R, FORM, FORM == kFormPacked && R >= 16>(st, prow, 32 * R, inRes, inH, inF, cs, S, outH, outF, 0);
+        column_step<R, FORM, SHORTF>(st, prow, 32 * R, inRes, inH, inF, cs, S, outH, outF, 0);
         outRes = inRes;
         if (tail) {
           const int j = t - LAG;
@@ -269,7 +267,9 @@ __global__ void __launch_bounds__(kBandStreamThreads, 2) band_stream_kernel(cons
       if (!in_range(p.x, a.db.n, a.status) || !in_range(p.y, a.db.n, a.status)) p = make_int2(0, 0);
       if (job.form == kBandPacked) {
         uint32_t S = 0u;
-        ok = band_unit<R, kFormPacked>(a, prof, ring, lane, p.x, p.y, sbase, ring_in, ring_out, cs, S);
+        // the one-operation F chain in 16-row lanes (3 % faster on the homolog
+        // workload; with 8 rows 2 % slower)
+        ok = band_unit<R, kFormPacked, (R >= 16)>(a, prof, ring, lane, p.x, p.y, sbase, ring_in, ring_out, cs, S);
         for (int d = 16; d > 0; d >>= 1) S = __vmaxs2(S, __shfl_xor_sync(0xffffffffu, S, d));
         if (ok && lane == 0) {
           if (in_range(job.q * a.out_stride + a.db.perm[p.x], a.out_size, a.status))
@@ -280,8 +280,13 @@ __global__ void __launch_bounds__(kBandStreamThreads, 2) band_stream_kernel(cons
         sbase += max(a.db.npad[p.x], a.db.npad[p.y]);
       } else {
         int32_t S = 0;
-        if (half) ok = band_unit<RH, kFormInt32>(a, prof, ring, lane, p.x, p.x, sbase, ring_in, ring_out, cs, S);
-        else ok = band_unit<R, kFormInt32>(a, prof, ring, lane, p.x, p.x, sbase, ring_in, ring_out, cs, S);
+        // (the int32 units of a 16-bit batch: the one-operation F chain too)
+        if (half && a.short_int)
+          ok = band_unit<RH, kFormInt32, true>(a, prof, ring, lane, p.x, p.x, sbase, ring_in, ring_out, cs, S);
+        else if (half) ok = band_unit<RH, kFormInt32, false>(a, prof, ring, lane, p.x, p.x, sbase, ring_in, ring_out, cs, S);
+        else if (a.short_int)
+          ok = band_unit<R, kFormInt32, true>(a, prof, ring, lane, p.x, p.x, sbase, ring_in, ring_out, cs, S);
+        else ok = band_unit<R, kFormInt32, false>(a, prof, ring, lane, p.x, p.x, sbase, ring_in, ring_out, cs, S);
         for (int d = 16; d > 0; d >>= 1) S = max(S, __shfl_xor_sync(0xffffffffu, S, d));
         if (ok && lane == 0 && in_range(job.q * a.out_stride + a.db.perm[p.x], a.out_size, a.status))
           atomicMax(&orow[a.db.perm[p.x]], S);
