@@ -509,7 +509,12 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
       any_track |= track_q[q] != 0;
     }
     int bocc = any_band ? band_max_ctas_per_sm(bR) : 1;
-    const int tocc = any_track ? track_max_ctas_per_sm(kTrackRows, kTrackSplit) : 1;
+    // transposed jobs beside band-stream jobs take 8-row lanes: twice the
+    // bands, each half the work per step, which fill in around the
+    // band-stream pipelines (homolog workload 2.29 -> 2.14 ms, A/B medians);
+    // alone (one short query) 16-row lanes are faster (0.081 against 0.084 ms)
+    const int tRows = any_band ? 8 : kTrackRows;
+    const int tocc = any_track ? track_max_ctas_per_sm(tRows, kTrackSplit) : 1;
     int64_t ring = 0, band = 0, tring = 0, tband = 0;
     if (bocc > 0 && tocc > 0) {
       // band jobs: each band query against every unit
@@ -614,7 +619,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
 
       // transposed jobs: the database in row tracks, each short query as columns
       if (any_track) {
-        const int tR = kTrackRows;
+        const int tR = tRows;
         const int32_t kRows = 32 * tR;  // rows per band
         int32_t mtq = 0;
         int64_t qt = 0;

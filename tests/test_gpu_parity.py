@@ -550,7 +550,8 @@ def test_band_stream_saturating_and_asymmetric(api, mode, rows):
 
 
 @pytest.mark.parametrize("mode", MODES)
-def test_transposed_jobs_int32_tracks_and_long_rows(api, mode):
+@pytest.mark.parametrize("with_band_query", [False, True])
+def test_transposed_jobs_int32_tracks_and_long_rows(api, mode, with_band_query):
     # transposed jobs (short queries: the database sequences are the rows):
     # with 512-row bands the queries below 1,024 residues run transposed; a
     # +60 identity-like matrix lets a 700-residue query pass the 16-bit range
@@ -558,7 +559,9 @@ def test_transposed_jobs_int32_tracks_and_long_rows(api, mode):
     # saturate against it go to int32 row tracks, the others two per word.
     # Copies of 5,000 residues span ten bands of one track (a pipeline); the
     # empty and one-residue sequences score 0 and the SM of query residue x
-    # database residue is asymmetric
+    # database residue is asymmetric.  with_band_query: a 1,100-residue query
+    # runs as band-stream jobs beside them, and the transposed jobs take
+    # 8-row lanes (256-row bands)
     rng = np.random.Generator(np.random.PCG64(514))
     sm = rng.integers(-9, 4, size=(20, 20)).astype(np.int8)
     np.fill_diagonal(sm, 60)
@@ -567,8 +570,10 @@ def test_transposed_jobs_int32_tracks_and_long_rows(api, mode):
     seqs[3], seqs[40], seqs[41], seqs[90] = base.copy(), base[:700].copy(), base[100:900].copy(), base[4000:]
     seqs[5], seqs[6] = np.zeros(0, np.uint8), base[:1].copy()
     db = from_list(seqs)
-    q = from_list([base[:700].copy(), base[50:200].copy(), rng.integers(0, 20, size=33).astype(np.uint8),
-                   np.zeros(0, np.uint8)])
+    ql = [base[:700].copy(), base[50:200].copy(), rng.integers(0, 20, size=33).astype(np.uint8), np.zeros(0, np.uint8)]
+    if with_band_query:
+        ql.append(base[1000:2100].copy())
+    q = from_list(ql)
     exp = oracle.scores(q, db, sm, 10, 2)
     assert exp.max() > 32767
     got = _search(api, db, q, mode, sm=sm, opts=api.options(band_stream="always", band_rows=16))
