@@ -604,7 +604,10 @@ def run_ours(args, w):
                               "queries)" if args.mode == "packed" else "inter_kernel, int32 form")
 
     extras = {}
-    if not args.no_extras and rank == 0:
+    # the side measurements (other configurations, serving, the CPU oracle)
+    # are single-GPU figures: taken at N = 1 only, so that a multi-GPU run
+    # holds its GPUs for the timed steps alone
+    if not args.no_extras and world == 1:
         xclk = Clocks(local)
         xclk.start()
         # alignments of each query's best hits (sw_traceback)
@@ -653,11 +656,11 @@ def run_ours(args, w):
             e2e["gather"] = "all-gather of the score slices (NCCL) inside the timed region"
 
     serving = None
-    if rank == 0 and args.serve_requests > 0 and not (args.queries or args.db_limit):
+    if world == 1 and args.serve_requests > 0 and not (args.queries or args.db_limit):
         serving = run_serving(args.serve_requests, args.serve_half_requests, args.mode, local)
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline:
         g, threads, c, dt = oracle_sample_gcups(w, 8000)
         g1, _, c1, dt1 = oracle_sample_gcups(w, 200, seed=4300, threads=1)
         cpu = {"value": round(g, 3), "unit": "GCUPS", "cores": threads, "kind": "oracle",
