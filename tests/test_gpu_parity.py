@@ -578,3 +578,32 @@ def test_transposed_jobs_int32_tracks_and_long_rows(api, mode, with_band_query):
     assert exp.max() > 32767
     got = _search(api, db, q, mode, sm=sm, opts=api.options(band_stream="always", band_rows=16))
     _assert_equal(got, exp)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_small_batch_plans_random(api, seed):
+    # random small batches through the small-batch plan (band-stream and
+    # transposed jobs, forced): database and query lengths from 0 to a few
+    # thousand (some databases with copies of a query, so that pairs pass the
+    # 16-bit range), random asymmetric matrices with a strong diagonal,
+    # random gap costs and both band heights; both forms, exact
+    rng = np.random.Generator(np.random.PCG64(9000 + seed))
+    sm = rng.integers(-8, 5, size=(20, 20)).astype(np.int8)
+    np.fill_diagonal(sm, rng.integers(4, 61, size=20))
+    go, ge = int(rng.integers(0, 16)), int(rng.integers(0, 5))
+    nq = int(rng.integers(1, 6))
+    qs = [rng.integers(0, 20, size=int(L)).astype(np.uint8)
+          for L in rng.choice([0, 1, 40, 144, 300, 700, 1100, 1700, 2600], size=nq)]
+    nd = int(rng.integers(1, 260))
+    seqs = [rng.integers(0, 20, size=int(min(3000, rng.lognormal(np.log(250), 0.9)))).astype(np.uint8)
+            for _ in range(nd)]
+    long_q = max(qs, key=len)
+    for k in range(min(3, nd)):  # copies of parts of the longest query
+        a = int(rng.integers(0, max(1, len(long_q))))
+        seqs[int(rng.integers(0, nd))] = long_q[a:a + int(rng.integers(1, 2500))].copy()
+    db, q = from_list(seqs), from_list(qs)
+    exp = oracle.scores(q, db, sm, go, ge)
+    rows = int(rng.choice([8, 16]))
+    for mode in MODES:
+        got = _search(api, db, q, mode, sm=sm, go=go, ge=ge, opts=api.options(band_stream="always", band_rows=rows))
+        _assert_equal(got, exp)
