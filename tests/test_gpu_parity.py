@@ -253,9 +253,10 @@ def test_homologs_precision_path(api, homologs, mode, cutover, band):
     # max(SM)*min(m, n) passes the 16-bit threshold); with cutover 16384 they
     # run packed in the inter-task kernel, saturate, are flagged and rescued
     # exactly.  With them (the default for this small batch): the
-    # 8,000-residue query runs in 32 bands against every unit, the homologs in
-    # int32, the others packed; the 144-residue query against the homologs in
-    # one band.
+    # 8,000-residue query runs in 16 bands of 512 rows against every unit
+    # (the homologs in int32, in 32 bands of 256 rows; the others two per
+    # word), the 144-residue query transposed against row tracks of every
+    # sequence.
     w = homologs
     db = api.Database.from_sequences(w["db"])
     pq = api.PreparedQueries(db, w["queries"].residues, w["queries"].offsets, BLOSUM62, 10, 2, mode,
