@@ -148,6 +148,7 @@ struct sw_queries {
   // other queries against the long units
   int64_t n_bjobs = 0, n_bands = 0, n_btargets = 0, band_ring_bytes = 0;
   int bgrid = 1, bR = 8;
+  bool bone = false;  // band-stream launch limited to one CTA per SM
   // transposed jobs (small batches): database row tracks against each short query
   int64_t n_tjobs = 0, n_tbands = 0, n_tlanes = 0, track_ring_bytes = 0, qt_bytes = 16;
   int tgrid = 1, tR = 16;
@@ -508,7 +509,8 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
       any_band |= band_q[q] != 0;
       any_track |= track_q[q] != 0;
     }
-    int bocc = any_band ? band_max_ctas_per_sm(bR) : 1;
+    const int bmax = any_band ? band_max_ctas_per_sm(bR) : 1;
+    int bocc = bmax;
     // transposed jobs beside band-stream jobs take 8-row lanes: twice the
     // bands, each half the work per step, which fill in around the
     // band-stream pipelines (homolog workload 2.29 -> 2.14 ms, A/B medians);
@@ -745,6 +747,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
         Q->bR = bR;
         Q->bgrid = (int)std::max<int64_t>(1, std::min<int64_t>((band + band_threads() / 32 - 1) / (band_threads() / 32),
                                                                (int64_t)sms * bocc));
+        Q->bone = bocc == 1 && bmax > 1;
         Q->n_tjobs = (int64_t)tjobs.size();
         Q->n_tbands = tband;
         Q->n_tlanes = (int64_t)tlanes.size();
@@ -1336,7 +1339,7 @@ int sw_search_prepared(const sw_db *db, const sw_queries *Q, int32_t *scores_dev
       ba.sc = Q->sc;
       ba.status = w + 2;
       ba.short_int = packed ? 1 : 0;
-      SW_CUDA(launch_band(ba, Q->bR, Q->bgrid, Q->side), "band-stream kernel");
+      SW_CUDA(launch_band(ba, Q->bR, Q->bgrid, Q->bone, Q->side), "band-stream kernel");
     }
     InterArgs b = a;
     b.qd = Q->d_qdi;

@@ -227,7 +227,8 @@ int band_threads();
 bool band_supported_R(int R);  // rows per lane: 8 or 16 (bands of 256 or 512 query rows)
 size_t band_smem_bytes(int R);
 int band_max_ctas_per_sm(int R);  // plan time: raises the shared-memory limit; 0 on failure
-cudaError_t launch_band(const BandArgs &a, int R, int grid, cudaStream_t s);
+// one_per_sm: reserve shared memory so that the launch places at most one CTA per SM
+cudaError_t launch_band(const BandArgs &a, int R, int grid, bool one_per_sm, cudaStream_t s);
 
 // Traceback of selected hits (k_trace.cu): one warp per hit fills 4-bit
 // provenance codes per cell, one thread per hit walks them back.

@@ -35,6 +35,7 @@
 // Scores: each band keeps its running best per unit and adds it to the
 // caller-order output with atomicMax (the host zeroes the jobs' output rows
 // first); the maximum over the bands is the unit's score.
+#include <algorithm>
 #include "devutil.cuh"
 #include "dp_common.cuh"
 #include "internal.h"
@@ -624,10 +625,26 @@ size_t smem_of() {
   return kSubmatBytes + (size_t)(kBandStreamThreads / 32) * kWarpBytes<R>;
 }
 
+// Dynamic shared memory that leaves room for only one band-stream CTA per SM
+// (more than half of an SM's shared memory), or 0 if a block may not take it.
+size_t one_cta_smem() {
+  int dev = 0, per_sm = 0, per_block = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const size_t want = ((size_t)per_sm / 2 + 1024 + 127) / 128 * 128;
+  return want <= (size_t)per_block ? want : 0;
+}
+
 template <int R>
 int occupancy_of() {
-  if (cudaFuncSetAttribute(band_stream_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem_of<R>()) != cudaSuccess) {
+  // the limit admits the one-CTA-per-SM reservation as well
+  const size_t limit = std::max(smem_of<R>(), one_cta_smem());
+  if (cudaFuncSetAttribute(band_stream_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit) !=
+      cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -686,9 +703,14 @@ bool band_supported_R(int R) { return R == 8 || R == 16; }
 size_t band_smem_bytes(int R) { return R == 16 ? smem_of<16>() : smem_of<8>(); }
 int band_max_ctas_per_sm(int R) { return R == 8 ? occupancy_of<8>() : R == 16 ? occupancy_of<16>() : 0; }
 
-cudaError_t launch_band(const BandArgs &a, int R, int grid, cudaStream_t s) {
-  if (R == 8) band_stream_kernel<8><<<grid, kBandStreamThreads, smem_of<8>(), s>>>(a);
-  else if (R == 16) band_stream_kernel<16><<<grid, kBandStreamThreads, smem_of<16>(), s>>>(a);
+cudaError_t launch_band(const BandArgs &a, int R, int grid, bool one_per_sm, cudaStream_t s) {
+  // one CTA per SM: the launch takes more than half of an SM's shared memory,
+  // so that the hardware never places two on an SM, whatever else (the
+  // transposed jobs beside it, a kernel finishing before it) holds the SMs
+  // when its CTAs are placed
+  const size_t extra = one_per_sm ? one_cta_smem() : 0;
+  if (R == 8) band_stream_kernel<8><<<grid, kBandStreamThreads, std::max(extra, smem_of<8>()), s>>>(a);
+  else if (R == 16) band_stream_kernel<16><<<grid, kBandStreamThreads, std::max(extra, smem_of<16>()), s>>>(a);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
