@@ -5,7 +5,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <mutex>
+#include <tuple>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -63,6 +66,67 @@ int sm_count(int dev) {
   return n > 0 ? n : 1;
 }
 
+// Launch occupancies depend only on the device, the kernel and its launch
+// shape, so each is asked of the runtime once per process (the query, and the
+// shared-memory attribute it sets, cost tens of microseconds per plan).
+// kind: 0 inter-task (a = R, b = form), 1 band-stream (a = R), 2 transposed
+// (a = R, b = split).  Failures (0) are not kept.
+int cached_occupancy(int kind, int a, int b, int threads, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int, int, int, size_t>, int> memo;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const auto key = std::make_tuple(dev, kind, a, b, threads, smem);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = memo.find(key);
+    if (it != memo.end()) return it->second;
+  }
+  const int n = kind == 0 ? inter_max_ctas_per_sm(a, b, threads, smem)
+                : kind == 1 ? band_max_ctas_per_sm(a)
+                            : track_max_ctas_per_sm(a, b != 0);
+  if (n > 0) {
+    std::lock_guard<std::mutex> lock(mu);
+    memo[key] = n;
+  }
+  return n;
+}
+
+// The stream-ordered pool that every query batch's device block comes from,
+// one per device, created on first use: freed blocks stay reserved up to
+// 1 GiB, so that planning a batch after another does not map fresh memory
+// (the default pool returns it at every synchronisation: ~0.1-0.2 ms per
+// plan).  Its own pool, so that the process's default pool keeps its settings.
+cudaError_t batch_pool(cudaMemPool_t *pool) {
+  static std::mutex mu;
+  static std::map<int, cudaMemPool_t> pools;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = pools.find(dev);
+  if (it != pools.end()) {
+    *pool = it->second;
+    return cudaSuccess;
+  }
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t p = nullptr;
+  e = cudaMemPoolCreate(&p, &props);
+  if (e != cudaSuccess) return e;
+  uint64_t keep = (uint64_t)1 << 30;
+  e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+  if (e != cudaSuccess) {
+    cudaMemPoolDestroy(p);
+    return e;
+  }
+  pools[dev] = p;
+  *pool = p;
+  return cudaSuccess;
+}
+
 int check_seqs(const uint8_t *res, const int64_t *off, int64_t n, const char *what) {
   if (n < 0) return fail(SW_EINVAL, "%s: negative sequence count", what);
   if (!off) return fail(SW_EINVAL, "%s: null offsets", what);
@@ -103,6 +167,30 @@ struct sw_db {
   // units (one sequence, or two consecutive ones in packed mode, the last
   // repeated when n is odd), shared by every query batch
   const int32_t *d_ident = nullptr;
+  // per mode (0 int32: one sequence per unit; 1 packed: two), built on first
+  // use: the count of units of each padded length / 16 and the prefix sums
+  // of the units' lengths, so that planning a batch does not walk every unit
+  struct UnitStats {
+    std::vector<int64_t> hist, prefix;
+  };
+  mutable std::mutex stats_mu;
+  mutable std::unique_ptr<UnitStats> unit_stats[2];
+  const UnitStats &units(bool packed) const {
+    std::lock_guard<std::mutex> lock(stats_mu);
+    std::unique_ptr<UnitStats> &u = unit_stats[packed ? 1 : 0];
+    if (!u) {
+      u.reset(new UnitStats());
+      const int64_t nu = packed ? (n + 1) / 2 : n;
+      u->hist.assign((size_t)max_npad / 16 + 1, 0);
+      u->prefix.assign((size_t)nu + 1, 0);
+      for (int64_t k = 0; k < nu; ++k) {
+        const int32_t len = h_npad[(size_t)std::min<int64_t>(packed ? 2 * k : k, n - 1)];
+        ++u->hist[(size_t)len / 16];
+        u->prefix[(size_t)k + 1] = u->prefix[(size_t)k] + len;
+      }
+    }
+    return *u;
+  }
 };
 
 struct sw_queries {
@@ -401,12 +489,18 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   Q->n_units = packed ? (n + 1) / 2 : n;
   auto unit_seq = [&](int64_t i) { return (int32_t)std::min<int64_t>(i, n - 1); };
   auto unit_len = [&](int64_t u) { return npad[unit_seq(packed ? 2 * u : u)]; };
-  int64_t n_long = 0;
-  while (n_long < Q->n_units && unit_len(n_long) >= cutover) ++n_long;
+  // (units are sorted by length, longest first: the long ones are a prefix)
+  int64_t n_long = 0, hi = Q->n_units;
+  while (n_long < hi) {
+    const int64_t mid = (n_long + hi) / 2;
+    if (unit_len(mid) >= cutover) n_long = mid + 1;
+    else hi = mid;
+  }
   Q->n_long = n_long;
+  static const sw_db::UnitStats kNoUnits{{0}, {0}};
+  const sw_db::UnitStats &ust = n > 0 ? db->units(packed) : kNoUnits;
   int32_t max_short = 16, max_long = 16;
-  double sum_short = 0;
-  for (int64_t u = n_long; u < Q->n_units; ++u) sum_short += unit_len(u);
+  const double sum_short = n > 0 ? (double)(ust.prefix[(size_t)Q->n_units] - ust.prefix[(size_t)n_long]) : 0.0;
   if (n_long < Q->n_units) max_short = unit_len(n_long);
   if (n_long) max_long = unit_len(0);
   // fill[L]: steps a chain of L lanes spends per real column of a short unit.
@@ -414,8 +508,11 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   // or 2 L - 1 for the split lanes of the 16-bit forms) rounded up to whole
   // 16-column blocks.  fill for the solo plans of this mode; fillq (below)
   // for the query-pair plans.
+  // (padded lengths are multiples of 16 and every long unit is longer than
+  // every short one, so the short units' counts are the first bins)
   std::vector<int64_t> len_hist(max_short / kColBlock + 1, 0);
-  for (int64_t u = n_long; u < Q->n_units; ++u) ++len_hist[unit_len(u) / kColBlock];
+  if (n_long < Q->n_units)
+    std::copy(ust.hist.begin(), ust.hist.begin() + std::min(len_hist.size(), ust.hist.size()), len_hist.begin());
   auto make_fill = [&](int form, double *out) {
     for (int L = 0; L <= 32; ++L) {
       const int lag = L > 0 ? inter_chain_lag(R, form, L) : 0;
@@ -509,14 +606,14 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
       any_band |= band_q[q] != 0;
       any_track |= track_q[q] != 0;
     }
-    const int bmax = any_band ? band_max_ctas_per_sm(bR) : 1;
+    const int bmax = any_band ? cached_occupancy(1, bR, 0, 0, 0) : 1;
     int bocc = bmax;
     // transposed jobs beside band-stream jobs take 8-row lanes: twice the
     // bands, each half the work per step, which fill in around the
     // band-stream pipelines (homolog workload 2.29 -> 2.14 ms, A/B medians);
     // alone (one short query) 16-row lanes are faster (0.081 against 0.084 ms)
     const int tRows = any_band ? 8 : kTrackRows;
-    const int tocc = any_track ? track_max_ctas_per_sm(tRows, kTrackSplit) : 1;
+    const int tocc = any_track ? cached_occupancy(2, tRows, kTrackSplit ? 1 : 0, 0, 0) : 1;
     int64_t ring = 0, band = 0, tring = 0, tband = 0;
     if (bocc > 0 && tocc > 0) {
       // band jobs: each band query against every unit
@@ -1017,10 +1114,13 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
       twp.push_back({t, (double)d.nchunks * d.L * d.R * (npad[s0 + i0] + d.L + 8)});
     }
   }
+  std::vector<size_t> tw_runs;  // start of each query's tiles in tw (each run is longest first already)
   for (int64_t q = 0; q < n_queries && Q->n_units > n_long; ++q) {
     if (in_track[q] || small_q[q]) continue;
     const QDesc &d = Q->qd[q];
     const int chains = warps * (32 / d.L);
+    tw_runs.push_back(tw.size());
+    tw.reserve(tw.size() + (size_t)((Q->n_units - n_long + chains - 1) / chains));
     for (int64_t u0 = n_long; u0 < Q->n_units; u0 += chains) {
       Task t{(int32_t)q, (int32_t)u0, (int32_t)std::min<int64_t>(chains, Q->n_units - u0), 0};
       tw.push_back({t, (double)d.nchunks * d.L * d.R * (unit_len(u0) + d.L + 8)});
@@ -1049,7 +1149,23 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
       }
     }
   }
-  std::stable_sort(tw.begin(), tw.end(), [](const TW &a, const TW &b) { return a.w > b.w; });
+  // all tiles longest first (ties in query order): the stable merge of the
+  // queries' runs, each already longest first (units are sorted), in place
+  // of a full sort of up to a few hundred thousand tiles
+  {
+    auto longer = [](const TW &a, const TW &b) { return a.w > b.w; };
+    tw_runs.push_back(tw.size());
+    while (tw_runs.size() > 2) {
+      std::vector<size_t> next;
+      for (size_t i = 0; i + 2 < tw_runs.size(); i += 2) {
+        std::inplace_merge(tw.begin() + tw_runs[i], tw.begin() + tw_runs[i + 1], tw.begin() + tw_runs[i + 2], longer);
+        next.push_back(tw_runs[i]);
+      }
+      if (tw_runs.size() % 2 == 0) next.push_back(tw_runs[tw_runs.size() - 2]);
+      next.push_back(tw_runs.back());
+      tw_runs.swap(next);
+    }
+  }
   std::stable_sort(twi.begin(), twi.end(), [](const TW &a, const TW &b) { return a.w > b.w; });
   std::stable_sort(twi32.begin(), twi32.end(), [](const TW &a, const TW &b) { return a.w > b.w; });
   // track tiles plan by plan (each plan's profile stays hot in L2 while the
@@ -1077,9 +1193,9 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
     delete Q;
     return fail(SW_EINVAL, "sw_queries_prepare: profile chunk too large for shared memory");
   }
-  const int occ = inter_max_ctas_per_sm(R, packed ? kFormPacked : kFormInt32, threads, Q->smem);
-  const int occ32 = inter_max_ctas_per_sm(R, kFormInt32, threads, Q->smem);
-  const int occp = Q->n_ptasks ? inter_max_ctas_per_sm(R, kFormQPair, threads, Q->psmem) : 1;
+  const int occ = cached_occupancy(0, R, packed ? kFormPacked : kFormInt32, threads, Q->smem);
+  const int occ32 = cached_occupancy(0, R, kFormInt32, threads, Q->smem);
+  const int occp = Q->n_ptasks ? cached_occupancy(0, R, kFormQPair, threads, Q->psmem) : 1;
   if (occ <= 0 || occ32 <= 0 || occp <= 0) {
     delete Q;
     return fail(SW_ECUDA, "sw_queries_prepare: cannot configure the inter-task kernel");
@@ -1136,7 +1252,9 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   Q->bytes = b_tjobs + b_tjobof + b_tlanes + b_qt + b_qtoff + b_qtnpad + b_trings + b_qres + b_sub + 2 * b_qd + b_tasks + b_itasks + b_itasks32 + b_ipos32 + b_rtasks + b_prof +
              b_gbuf + b_igbuf + b_words + b_flag + b_iflag + b_qdp + b_ptasks + b_track + b_bjobs + b_bjobof +
              b_btpos + b_brings;
-  cudaError_t e = cudaMallocAsync(&Q->block, Q->bytes, s);
+  cudaMemPool_t pool = nullptr;
+  cudaError_t e = batch_pool(&pool);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&Q->block, Q->bytes, pool, s);
   if (e != cudaSuccess) {
     delete Q;
     return cuda_fail(e, "sw_queries_prepare: device allocation");
