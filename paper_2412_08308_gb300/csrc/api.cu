@@ -426,6 +426,42 @@ int sw_db_stats(const sw_db *db, int64_t *n_seqs, int64_t *residues, int64_t *de
   return SW_OK;
 }
 
+namespace {
+
+// a DP task and its modelled cost (tasks are sorted longest first)
+struct TW {
+  Task t;
+  double w;
+};
+
+// The planner's large host tables, one set per thread, emptied at the start
+// of each plan but keeping their memory.
+struct PlanScratch {
+  std::vector<BandJob> bjobs;
+  std::vector<int32_t> bjob_of;
+  std::vector<int2> btpos;
+  std::vector<TrackJob> tjobs;
+  std::vector<int32_t> tjob_of;
+  std::vector<TrackLane> tlanes;
+  std::vector<TW> tw;
+  std::vector<Task> tasks;
+};
+
+PlanScratch &plan_scratch() {
+  static thread_local PlanScratch ps;
+  ps.bjobs.clear();
+  ps.bjob_of.clear();
+  ps.btpos.clear();
+  ps.tjobs.clear();
+  ps.tjob_of.clear();
+  ps.tlanes.clear();
+  ps.tw.clear();
+  ps.tasks.clear();
+  return ps;
+}
+
+}  // namespace
+
 int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int64_t n_queries,
                        const int8_t *submat, int32_t gap_open, int32_t gap_extend, int32_t mode,
                        const sw_options *opts, void *stream, sw_queries **out) {
@@ -588,12 +624,16 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   // entry per column between consecutive bands) do not fit a memory budget,
   // the batch takes the regular plan.
   std::vector<char> band_q(n_queries, 0), track_q(n_queries, 0), small_q(n_queries, 0);
-  std::vector<BandJob> bjobs;
-  std::vector<int32_t> bjob_of;
-  std::vector<int2> btpos;
-  std::vector<TrackJob> tjobs;
-  std::vector<int32_t> tjob_of;
-  std::vector<TrackLane> tlanes;
+  // (the planner's large tables live in per-thread buffers that keep their
+  // memory from one plan to the next: fresh allocations of a few hundred KB
+  // each cost their page faults again, ~0.2-0.8 ms per plan)
+  PlanScratch &scratch = plan_scratch();
+  std::vector<BandJob> &bjobs = scratch.bjobs;
+  std::vector<int32_t> &bjob_of = scratch.bjob_of;
+  std::vector<int2> &btpos = scratch.btpos;
+  std::vector<TrackJob> &tjobs = scratch.tjobs;
+  std::vector<int32_t> &tjob_of = scratch.tjob_of;
+  std::vector<TrackLane> &tlanes = scratch.tlanes;
   std::vector<int64_t> qt_off(std::max<int64_t>(n_queries, 1), 0);
   std::vector<int32_t> qt_npad(std::max<int64_t>(n_queries, 1), 16);
   bool band_mode = false;
@@ -737,81 +777,74 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
         // bands with room), so those bands depend on no other band.  Empty
         // sequences score 0 without a job.
         struct Seg {
-          int32_t pos, row0, rows;
+          int32_t pos, row0, rows, bin;  // sequence, first row in its track, rows (whole lanes), track
         };
-        std::vector<std::vector<Seg>> trk[2];  // [0] two per word (16-bit), [1] int32
-        std::vector<int32_t> fill[2];          // rows used in each track
+        std::vector<Seg> seg[2];          // [0] two per word (16-bit), [1] int32; in placement order
+        std::vector<int32_t> used[2];     // rows used in each track
         for (int64_t k = 0; k < n; ++k) {
           const int32_t len = db->h_len[k];
           if (len == 0) continue;
           const int f = (packed && (int64_t)sc.maxp * std::min<int32_t>(len, mtq) <= sc.thresh) ? 0 : 1;
           const int32_t rows = (int32_t)round_up(len, tR);
-          auto &T = trk[f];
-          auto &U = fill[f];
+          std::vector<int32_t> &U = used[f];
           if (rows > kRows) {
-            T.push_back({{(int32_t)k, 0, rows}});
+            seg[f].push_back({(int32_t)k, 0, rows, (int32_t)U.size()});
             U.push_back(rows);
             continue;
           }
-          size_t i = T.size();
-          for (size_t j = T.size() > 64 ? T.size() - 64 : 0; j < T.size(); ++j)
+          size_t i = U.size();
+          for (size_t j = U.size() > 64 ? U.size() - 64 : 0; j < U.size(); ++j)
             if (U[j] <= kRows - rows) {
               i = j;
               break;
             }
-          if (i == T.size()) {
-            T.push_back({});
-            U.push_back(0);
-          }
-          T[i].push_back({(int32_t)k, U[i], rows});
+          if (i == U.size()) U.push_back(0);
+          seg[f].push_back({(int32_t)k, U[i], rows, (int32_t)i});
           U[i] += rows;
         }
-        // pipelines: packed ones pair tracks of equal band counts (longest first)
-        auto bands_of = [&](const std::vector<Seg> &t) {
-          const Seg &g = t.back();
-          return (int32_t)((g.row0 + g.rows + kRows - 1) / kRows);
-        };
-        for (int f = 0; f < 2; ++f)
-          std::stable_sort(trk[f].begin(), trk[f].end(), [&](const std::vector<Seg> &x, const std::vector<Seg> &y) {
-            return bands_of(x) > bands_of(y);
-          });
-        // the lane table of a pipeline: band b, lane l covers rows b * 32R + l R .. + R - 1
-        // (rows visited in increasing order, so each track's segment cursor only advances;
-        // a bin's segments are in placement order, which is by row)
-        auto lane_of = [&](const std::vector<Seg> *t, size_t &cur, int64_t row, int32_t &pos, int32_t &r0) {
-          pos = -1;
-          r0 = 0;
-          if (!t) return;
-          while (cur < t->size() && row >= (*t)[cur].row0 + (*t)[cur].rows) ++cur;
-          if (cur < t->size() && row >= (*t)[cur].row0) {
-            pos = (*t)[cur].pos;
-            r0 = (int32_t)(row - (*t)[cur].row0);
-          }
-        };
+        // pipelines: the tracks ordered by band count (longest first); packed
+        // ones pair consecutive tracks.  The lane table of a pipeline: band b,
+        // lane l covers rows (32 b + l) R .. + R - 1 of its track(s); each
+        // segment writes its own lanes (whole lanes from a lane boundary), the
+        // others stay idle
         struct Pipe {
           int32_t packed, nb, lane0;
         };
         std::vector<Pipe> pipes;
         for (int f = 0; f < 2; ++f) {
-          auto &T = trk[f];
-          for (auto &t : T)  // segments by row for the cursor walk
-            std::sort(t.begin(), t.end(), [](const Seg &x, const Seg &y) { return x.row0 < y.row0; });
-          const size_t step = f == 0 ? 2 : 1;
-          for (size_t i = 0; i < T.size(); i += step) {
-            const std::vector<Seg> *ta = &T[i];
-            const std::vector<Seg> *tb = (f == 0 && i + 1 < T.size()) ? &T[i + 1] : nullptr;
-            const int32_t nb = std::max(bands_of(*ta), tb ? bands_of(*tb) : 1);
+          const std::vector<int32_t> &U = used[f];
+          const int32_t B = (int32_t)U.size();
+          auto bands = [&](int32_t t) { return (int32_t)((U[t] + kRows - 1) / kRows); };
+          std::vector<int32_t> order(B), base(B), high(B);
+          std::iota(order.begin(), order.end(), 0);
+          std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return bands(x) > bands(y); });
+          const int32_t step = f == 0 ? 2 : 1;
+          for (int32_t i = 0; i < B; i += step) {
+            const int32_t ta = order[i], tb = (f == 0 && i + 1 < B) ? order[i + 1] : -1;
+            const int32_t nb = std::max(bands(ta), tb >= 0 ? bands(tb) : 1);
             Pipe pp{f == 0 ? 1 : 0, nb, (int32_t)tlanes.size()};
-            size_t ca = 0, cb = 0;
-            for (int32_t b = 0; b < nb; ++b)
-              for (int l = 0; l < 32; ++l) {
-                TrackLane L{};
-                const int64_t row = (int64_t)b * kRows + (int64_t)l * tR;
-                lane_of(ta, ca, row, L.pa, L.ra);
-                lane_of(tb, cb, row, L.pb, L.rb);
-                tlanes.push_back(L);
-              }
+            base[ta] = pp.lane0;
+            high[ta] = 0;
+            if (tb >= 0) {
+              base[tb] = pp.lane0;
+              high[tb] = 1;
+            }
+            tlanes.resize(tlanes.size() + 32 * (size_t)nb, TrackLane{-1, 0, -1, 0});
             pipes.push_back(pp);
+          }
+          for (const Seg &g : seg[f]) {
+            TrackLane *L = tlanes.data() + base[g.bin] + g.row0 / tR;
+            if (high[g.bin]) {
+              for (int32_t k = 0; k < g.rows / tR; ++k) {
+                L[k].pb = g.pos;
+                L[k].rb = k * tR;
+              }
+            } else {
+              for (int32_t k = 0; k < g.rows / tR; ++k) {
+                L[k].pa = g.pos;
+                L[k].ra = k * tR;
+              }
+            }
           }
         }
         // deeper pipelines first
@@ -1097,11 +1130,8 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   Q->ppbuf_bytes = (int)round_up(maxcp, 128);
 
   // --- tasks, longest first
-  struct TW {
-    Task t;
-    double w;
-  };
-  std::vector<TW> tw, twi, twi32, twp;
+  std::vector<TW> twi, twi32, twp;
+  std::vector<TW> &tw = scratch.tw;
   std::vector<int32_t> ipos32;  // database positions of the int32 intra-task units
   int64_t rcap = 0;
   // (a pair of sequences scores at most max(SM) * min(m, n): a packed lane
@@ -1299,7 +1329,9 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   Q->d_upos = const_cast<int32_t *>(db->d_ident) + s0;  // the short sequences, in sorted order
   Q->n_upos = n + 1 - s0;
 
-  std::vector<Task> tasks(Q->n_tasks), itasks(Q->n_itasks), itasks32(Q->n_itasks32), ptasks(Q->n_ptasks);
+  std::vector<Task> &tasks = scratch.tasks;
+  tasks.resize((size_t)Q->n_tasks);
+  std::vector<Task> itasks(Q->n_itasks), itasks32(Q->n_itasks32), ptasks(Q->n_ptasks);
   for (int64_t i = 0; i < Q->n_ptasks; ++i) ptasks[i] = twp[i].t;
   for (int64_t i = 0; i < Q->n_tasks; ++i) tasks[i] = tw[i].t;
   for (int64_t i = 0; i < Q->n_itasks; ++i) itasks[i] = twi[i].t;
