@@ -138,6 +138,13 @@ typedef struct sw_options {
  *   stream                          upload stream; the call returns after it completes
  *   out                             receives the new handle
  *
+ * Memory: the batch's device scratch is one block from a stream-ordered
+ * memory pool that the library creates for each device on first use (not
+ * the device's default pool); blocks freed by sw_queries_free stay reserved
+ * in that pool, up to 1 GiB, for later batches.  The planner keeps its host
+ * tables in per-thread buffers between calls.  Calls from several threads
+ * are safe.
+ *
  * Errors: SW_EINVAL (bad arguments or knobs), SW_ENOMEM, SW_ECUDA.
  */
 int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q_offsets,
