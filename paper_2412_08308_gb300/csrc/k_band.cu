@@ -44,7 +44,13 @@
 namespace swgb {
 namespace {
 
-constexpr int kBandStreamThreads = 256;  // 8 warps, one band at a time each
+// 12 warps, one band at a time each, one CTA per SM with up to 168
+// registers a thread (the 512-row bands' profiles take 134 KB of shared
+// memory).  Homolog workload, ms per search (packed / int32): 8 warps at 128
+// registers (one or two CTAs per SM) 2.14 / 3.43; 10 warps 2.15 / 3.71; 12
+// warps 1.95 / 3.31 (2.10 / 3.28 capped at 128 registers); 14 warps 2.33 /
+// 3.50; 16 warps 2.37 / 3.25.
+constexpr int kBandStreamThreads = 384;
 constexpr int kLag = 32 - 1;  // a band's last lane trails its first by 31 columns
 constexpr int kSubmatBytes = 512;
 // R rows per lane: bands of 32 R query rows; a band's profile is [21][32 lanes
@@ -233,7 +239,7 @@ __device__ __forceinline__ bool band_unit(const BandArgs &a, const uint8_t *__re
 }
 
 template <int R>
-__global__ void __launch_bounds__(kBandStreamThreads, 2) band_stream_kernel(const BandArgs a) {
+__global__ void __launch_bounds__(kBandStreamThreads, 1) band_stream_kernel(const BandArgs a) {
   constexpr int RH = R / 2;  // rows per lane of kBandInt32Half jobs
   extern __shared__ __align__(128) uint8_t smem[];
   int8_t *sm = reinterpret_cast<int8_t *>(smem);
