@@ -700,8 +700,9 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
       // sets the pace of the launch: it runs in bands of half the height
       // (half the work per step; its steps run one after the other), and if
       // its steps, slowed by the other warps that share its SM sub-partition
-      // (two per CTA per SM, all computing), would outlast the launch's
-      // average load, the launch keeps one CTA per SM instead of two.
+      // (those of every CTA on the SM, all computing), would outlast the
+      // launch's average load, the launch keeps one CTA per SM (a choice
+      // only for band heights whose CTAs fit twice on an SM).
       constexpr double kWaves = 2.0;
       const int wpc = band_threads() / 32;  // warps per CTA
       auto per_warp_at = [&](int occ) {

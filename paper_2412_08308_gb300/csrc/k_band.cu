@@ -14,9 +14,11 @@
 // short enough (a few thousand columns) that many jobs run at once, and every
 // unit's cells are spread over all the job's warps instead of one.
 //
-// Forms: int32 cells (one database sequence per unit, Algorithm 1's
-// statements) or two sequences per unit in the 16-bit halves of a word (only
-// for pairs that cannot pass the 16-bit range, so no rescue is needed).  A
+// Forms: int32 cells, one database sequence per unit (Algorithm 1's
+// statements in int32 batches; in 16-bit batches, for the pairs that could
+// pass the 16-bit range, the one-operation F chain), or two sequences per
+// unit in the 16-bit halves of a word (only for pairs that cannot pass the
+// 16-bit range, so no rescue is needed).  A
 // lane's R rows form one chain down the column (no split lanes: the pipeline
 // lag between consecutive bands is then 31 columns instead of 63, which
 // measured faster here, where several bands share each SM sub-partition).
