@@ -653,7 +653,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
     // band-stream pipelines (homolog workload 2.29 -> 2.14 ms, A/B medians);
     // alone (one short query) 16-row lanes are faster (0.081 against 0.084 ms)
     const int tRows = any_band ? 8 : kTrackRows;
-    const int tocc = any_track ? cached_occupancy(2, tRows, kTrackSplit ? 1 : 0, 0, 0) : 1;
+    int tocc = any_track ? cached_occupancy(2, tRows, kTrackSplit ? 1 : 0, 0, 0) : 1;
     int64_t ring = 0, band = 0, tring = 0, tband = 0;
     if (bocc > 0 && tocc > 0) {
       // band jobs: each band query against every unit
@@ -758,30 +758,33 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
       }
 
       // transposed jobs: the database in row tracks, each short query as columns
-      if (any_track) {
-        const int tR = tRows;
+      struct Seg {
+        int32_t pos, row0, rows, bin;  // sequence, first row in its track, rows (whole lanes), track
+      };
+      int32_t mtq = 0;
+      int64_t qt = 0;
+      int64_t n_track_q = 0;
+      for (int64_t q = 0; q < n_queries; ++q) {
+        if (!track_q[q]) continue;
+        ++n_track_q;
+        mtq = std::max(mtq, qlen(q));
+        qt_npad[q] = (int32_t)std::max<int64_t>(kColBlock, round_up(qlen(q), kColBlock));
+        qt_off[q] = qt;
+        qt += qt_npad[q];
+      }
+      Q->qt_bytes = std::max<int64_t>(qt, 16);
+      // tracks: a sequence longer than a band gets a track of its own (its
+      // bands run as a pipeline); the others, each padded to whole lanes,
+      // are packed into one-band tracks without crossing a band boundary
+      // (sorted longest first, each into the first of the last 64 open
+      // bands with room), so those bands depend on no other band.  Empty
+      // sequences score 0 without a job.
+      auto bin_tracks = [&](const int tR, std::vector<Seg> (&seg)[2], std::vector<int32_t> (&used)[2]) {
         const int32_t kRows = 32 * tR;  // rows per band
-        int32_t mtq = 0;
-        int64_t qt = 0;
-        for (int64_t q = 0; q < n_queries; ++q) {
-          if (!track_q[q]) continue;
-          mtq = std::max(mtq, qlen(q));
-          qt_npad[q] = (int32_t)std::max<int64_t>(kColBlock, round_up(qlen(q), kColBlock));
-          qt_off[q] = qt;
-          qt += qt_npad[q];
+        for (int f = 0; f < 2; ++f) {
+          seg[f].clear();
+          used[f].clear();
         }
-        Q->qt_bytes = std::max<int64_t>(qt, 16);
-        // tracks: a sequence longer than a band gets a track of its own (its
-        // bands run as a pipeline); the others, each padded to whole lanes,
-        // are packed into one-band tracks without crossing a band boundary
-        // (sorted longest first, each into the first of the last 64 open
-        // bands with room), so those bands depend on no other band.  Empty
-        // sequences score 0 without a job.
-        struct Seg {
-          int32_t pos, row0, rows, bin;  // sequence, first row in its track, rows (whole lanes), track
-        };
-        std::vector<Seg> seg[2];          // [0] two per word (16-bit), [1] int32; in placement order
-        std::vector<int32_t> used[2];     // rows used in each track
         for (int64_t k = 0; k < n; ++k) {
           const int32_t len = db->h_len[k];
           if (len == 0) continue;
@@ -803,6 +806,27 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
           seg[f].push_back({(int32_t)k, U[i], rows, (int32_t)i});
           U[i] += rows;
         }
+      };
+      // bands of all transposed jobs: the tracks ordered by band count
+      // (longest first), packed ones paired, each pipeline once per query
+      auto count_bands = [&](const int tR, const std::vector<int32_t> (&used)[2]) {
+        const int32_t kRows = 32 * tR;
+        int64_t total = 0;
+        for (int f = 0; f < 2; ++f) {
+          std::vector<int32_t> nb(used[f].size());
+          for (size_t t = 0; t < nb.size(); ++t) nb[t] = (used[f][t] + kRows - 1) / kRows;
+          std::sort(nb.begin(), nb.end(), std::greater<int32_t>());
+          for (size_t i = 0; i < nb.size(); i += (f == 0 ? 2 : 1)) total += nb[i];
+        }
+        return total * n_track_q;
+      };
+      auto build_tracks = [&](const int tR, const std::vector<Seg> (&seg)[2], const std::vector<int32_t> (&used)[2]) {
+        const int32_t kRows = 32 * tR;
+        tjobs.clear();
+        tjob_of.clear();
+        tlanes.clear();
+        tring = 0;
+        tband = 0;
         // pipelines: the tracks ordered by band count (longest first); packed
         // ones pair consecutive tracks.  The lane table of a pipeline: band b,
         // lane l covers rows (32 b + l) R .. + R - 1 of its track(s); each
@@ -865,6 +889,37 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
             tband += pp.nb;
             tjobs.push_back(j);
           }
+      };
+      if (any_track) {
+        // one wave of 16-row bands that leaves some SM sub-partitions two
+        // bands: 24-row lanes (768-row bands, one CTA of 4 warps per SM) when
+        // their bands then fit one per sub-partition -- each band's steps no
+        // longer share the issue slots.  One 144-residue query x 2,000
+        // proteins, packed: 0.081-0.085 -> 0.066 ms (32-row lanes the same);
+        // int32 (twice the bands) and larger databases stay at 16 rows
+        // (8,000 proteins: 0.189 ms at 16 rows, 0.228 at 24)
+        std::vector<Seg> seg[2];
+        std::vector<int32_t> used[2];
+        int tR = tRows;
+        bin_tracks(tR, seg, used);
+        const int64_t subparts = 4 * (int64_t)sms;
+        const int64_t bands16 = (!any_band && tRows == 16) ? count_bands(16, used) : 0;
+        if (bands16 > subparts && bands16 <= subparts * tocc) {
+          const int occ24 = cached_occupancy(2, 24, 0, 0, 0);
+          std::vector<Seg> seg24[2];
+          std::vector<int32_t> used24[2];
+          if (occ24 > 0) bin_tracks(24, seg24, used24);
+          const int64_t bands24 = occ24 > 0 ? count_bands(24, used24) : 0;
+          if (occ24 > 0 && bands24 <= subparts && bands24 <= (int64_t)sms * occ24 * (track_threads() / 32)) {
+            tR = 24;
+            tocc = occ24;
+            for (int f = 0; f < 2; ++f) {
+              seg[f].swap(seg24[f]);
+              used[f].swap(used24[f]);
+            }
+          }
+        }
+        build_tracks(tR, seg, used);
         Q->tR = tR;
       }
       const int64_t kBandRingBudget = (int64_t)4 << 30;

@@ -566,7 +566,7 @@ __device__ __forceinline__ void track_scores(const TrackArgs &a, int32_t q, int3
 }
 
 template <int R, bool SPLIT>
-__global__ void __launch_bounds__(kTrackThreads, R == 8 ? 4 : 2) band_track_kernel(const TrackArgs a) {
+__global__ void __launch_bounds__(kTrackThreads, R == 8 ? 4 : R == 16 ? 2 : 1) band_track_kernel(const TrackArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   int8_t *sm = reinterpret_cast<int8_t *>(smem);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -688,11 +688,12 @@ int track_occupancy() {
 
 int track_threads() { return kTrackThreads; }
 
-bool track_supported_R(int R) { return R == 8 || R == 16; }
+bool track_supported_R(int R) { return R == 8 || R == 16 || R == 24; }
 
 int track_max_ctas_per_sm(int R, bool split) {
   if (R == 8) return split ? track_occupancy<8, true>() : track_occupancy<8, false>();
   if (R == 16) return split ? track_occupancy<16, true>() : track_occupancy<16, false>();
+  if (R == 24 && !split) return track_occupancy<24, false>();
   return 0;
 }
 
@@ -702,6 +703,7 @@ cudaError_t launch_track(const TrackArgs &a, int R, bool split, int grid, cudaSt
   else if (R == 8) band_track_kernel<8, false><<<grid, T, track_smem<8>(), s>>>(a);
   else if (R == 16 && split) band_track_kernel<16, true><<<grid, T, track_smem<16>(), s>>>(a);
   else if (R == 16) band_track_kernel<16, false><<<grid, T, track_smem<16>(), s>>>(a);
+  else if (R == 24 && !split) band_track_kernel<24, false><<<grid, T, track_smem<24>(), s>>>(a);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
