@@ -608,3 +608,21 @@ def test_small_batch_plans_random(api, seed):
     for mode in MODES:
         got = _search(api, db, q, mode, sm=sm, go=go, ge=ge, opts=api.options(band_stream="always", band_rows=rows))
         _assert_equal(got, exp)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_transposed_24_row_lanes_edges(api, mode):
+    # one short query against ~2,000 proteins, the shape for which the
+    # packed plan takes 24-row lanes (768-row bands, one per SM
+    # sub-partition), with sequences at the lane and band edges of both
+    # heights (16/24-row lanes, 512/768-row bands) and longer than a band
+    rng = np.random.Generator(np.random.PCG64(515))
+    db_s = random_sequences(516, 1990, 300, 0.5, 20, 1000).as_list()
+    for L in (1, 15, 16, 17, 23, 24, 25, 47, 48, 49, 511, 512, 513, 767, 768, 769, 1023, 1024, 1025, 1536, 1537,
+              2300, 3000):
+        db_s.append(rng.integers(0, 20, size=L).astype(np.uint8))
+    rng.shuffle(db_s)
+    db = from_list(db_s)
+    q = from_list([rng.integers(0, 20, size=144).astype(np.uint8)])
+    got = _search(api, db, q, mode)
+    _assert_equal(got, oracle.scores(q, db, BLOSUM62, 10, 2))
