@@ -453,19 +453,24 @@ def test_bad_options_rejected(api):
 
 
 @pytest.mark.parametrize("mode", MODES)
-def test_graph_replay_matches(api, mode):
+@pytest.mark.parametrize("band", ["never", "always"])
+def test_graph_replay_matches(api, mode, band):
     # the whole search captured in a CUDA graph (long units included, so the
     # side-stream fork/join is captured too) and replayed twice, then again
-    # into a different output buffer (re-capture)
+    # into a different output buffer (re-capture); with the inter- and
+    # intra-task kernels, and with the small-batch plan (band-stream jobs on
+    # the side stream for the 1,100-residue query, transposed jobs beside)
     import torch
 
     rng = np.random.Generator(np.random.PCG64(61))
     lens = list(rng.integers(1, 600, size=120)) + [2500, 3100]
     db_s = from_list([rng.integers(0, 20, size=int(L)).astype(np.uint8) for L in lens])
-    q_s = random_sequences(62, 5, 300, 0.5, 1, 1500)
+    q_s = from_list(random_sequences(62, 5, 300, 0.5, 1, 1500).as_list() +
+                    [rng.integers(0, 20, size=1100).astype(np.uint8)])
     exp = oracle.scores(q_s, db_s, BLOSUM62, 10, 2)
     db = api.Database.from_sequences(db_s)
-    pq = api.PreparedQueries(db, q_s.residues, q_s.offsets, BLOSUM62, 10, 2, mode, opts=api.options(cutover=2048))
+    pq = api.PreparedQueries(db, q_s.residues, q_s.offsets, BLOSUM62, 10, 2, mode,
+                             opts=api.options(cutover=2048, band_stream=band))
     st = torch.cuda.Stream()
     with torch.cuda.stream(st):
         out = torch.full((len(q_s), len(db_s)), -1, dtype=torch.int32, device="cuda")
