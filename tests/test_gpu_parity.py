@@ -631,3 +631,39 @@ def test_transposed_24_row_lanes_edges(api, mode):
     q = from_list([rng.integers(0, 20, size=144).astype(np.uint8)])
     got = _search(api, db, q, mode)
     _assert_equal(got, oracle.scores(q, db, BLOSUM62, 10, 2))
+
+
+def test_searches_from_several_threads(api):
+    # plans and searches from four host threads at once on one database
+    # (per-thread planner tables, the shared occupancy cache, the memory
+    # pool and the database's unit statistics), small-batch and inter-task
+    # plans, each result exact
+    import threading
+
+    db_s = random_sequences(91, 1500, 300, 0.5, 1, 1200)
+    db = api.Database.from_sequences(db_s)
+    cases = [random_sequences(92 + i, n, 250, 0.6, 1, 1400) for i, n in enumerate((1, 3, 2, 9))]
+    exp = [oracle.scores(q, db_s, BLOSUM62, 10, 2) for q in cases]
+    got = [None] * len(cases)
+    errors = []
+
+    def run(i):
+        try:
+            import torch
+
+            with torch.cuda.stream(torch.cuda.Stream()):
+                for mode in ("packed", "int32"):
+                    r = api.search(db, cases[i].residues, cases[i].offsets, BLOSUM62, 10, 2, mode)
+                    got[i] = r if mode == "packed" else got[i]
+                    if not np.array_equal(r, exp[i]):
+                        errors.append((i, mode))
+        except Exception as e:  # noqa: BLE001 - reported below
+            errors.append((i, repr(e)))
+
+    threads = [threading.Thread(target=run, args=(i,)) for i in range(len(cases))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    db.close()
+    assert not errors, errors
