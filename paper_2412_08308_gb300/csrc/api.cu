@@ -606,20 +606,23 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   // --- small batches: band-stream jobs and transposed jobs (k_band.cu).  In
   // a batch too small to fill the GPU, the longest chains of the inter-task
   // kernel set the time while most SMs idle, so:
-  //  - a query of at least two bands (512 rows) runs against every database
-  //    unit as pipelines of 256-row bands, one warp each: a job is one query
-  //    and a stream of units, all its bands sweeping the stream together.  A
-  //    unit whose pair with the query could pass the 16-bit range is split
-  //    into its sequences in int32; the others keep two sequences per word.
-  //    Streams are cut so that every warp of one launch gets about the same
-  //    number of columns (the longest unit at least);
+  //  - a query of at least two bands (2 x 32 x band_rows rows; 1,024 with the
+  //    default 16 rows per lane) runs against every database unit as
+  //    pipelines of bands, one warp each: a job is one query and a stream of
+  //    units, all its bands sweeping the stream together.  A unit whose pair
+  //    with the query could pass the 16-bit range is split into its
+  //    sequences in int32; the others keep two sequences per word.  Streams
+  //    are cut so that every warp of one launch gets about two jobs' worth
+  //    of columns (one unit at least);
   //  - every shorter query runs transposed: the database sequences are the
-  //    rows, stacked in row tracks of whole 8-row lanes, and the query the
-  //    columns; each band of a track is one warp, several short sequences
-  //    share a band, and the bands of a longer one run as a pipeline.  In
-  //    packed mode two tracks share each word (one query residue per column:
-  //    query-pair words), except sequences whose pair with the longest of
-  //    these queries could pass the 16-bit range (int32 tracks).
+  //    rows, stacked in row tracks of whole lanes (16 rows; 8 beside
+  //    band-stream jobs; 24 when that gives one band per SM sub-partition),
+  //    and the query the columns; each band of a track is one warp, several
+  //    short sequences share a band, and the bands of a longer one run as a
+  //    pipeline.  In packed mode two tracks share each word (their
+  //    substitution bytes paired per row), except sequences whose pair with
+  //    the longest of these queries could pass the 16-bit range (int32
+  //    tracks).
   // The inter- and intra-task kernels are then not used.  If the rings (one
   // entry per column between consecutive bands) do not fit a memory budget,
   // the batch takes the regular plan.
