@@ -114,7 +114,7 @@ typedef struct sw_options {
                               rows cut into bands, one warp each, the bands of a query running
                               as a pipeline over a stream of units; every shorter query
                               transposed, the database sequences stacked as rows in bands of
-                              512 rows and the query's residues as the columns; 1 = never;
+                              256 to 768 rows and the query's residues as the columns; 1 = never;
                               2 = for every batch, however large */
   int32_t band_rows;       /* query rows per lane of the band-stream kernel: 8 or 16 (bands of
                               256 or 512 rows); 0 = 16 */
