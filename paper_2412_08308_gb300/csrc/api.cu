@@ -58,6 +58,10 @@ inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 // column apart or not
 constexpr int kTrackRows = 16;
 constexpr bool kTrackSplit = false;
+// packed mode: the solo queries' profiles hold 32-bit entries, so that the
+// two-sequence form pairs them by a multiply-add on the FMA pipe instead of
+// a byte shuffle on the ALU pipe (the int32 rescue reads the same entries)
+constexpr bool kWideSolo = true;
 
 
 int sm_count(int dev) {
@@ -207,6 +211,7 @@ struct sw_queries {
   int64_t npairs = 0, n_ptasks = 0, n_solo = 0, n_single = 0;
   bool inter_may_flag = false;  // some packed inter-task pair can exceed the 16-bit threshold
   int grid = 1, rgrid = 1, igrid = 1, pgrid = 1, threads = 256;
+  int solo_form = kFormPacked, rescue_form = kFormInt32;  // forms (with kFormWide) of the solo and rescue launches
   int pbuf_bytes = 0, ipbuf_bytes = 0, ppbuf_bytes = 0;
   int pbuf_count = 2, ppbuf_count = 2;  // profile buffers of the two inter-task launches
   size_t smem = 0, ismem = 0, psmem = 0;
@@ -1109,7 +1114,8 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
     d.L = pick_lanes(std::max(1, d.m), 32);
     const int LR = d.L * R;
     d.nchunks = std::max(1, (d.m + LR - 1) / LR);
-    d.chunk_stride = (int32_t)round_up((int64_t)profile_slots(d.L) * R, 128);
+    d.wide = packed && kWideSolo ? 1 : 0;
+    d.chunk_stride = (int32_t)round_up((int64_t)profile_slots(d.L) * R * (d.wide ? 4 : 1), 128);
     d.chunk_bytes = (in_track[q] || small_q[q]) ? 0 : kProfRows * d.chunk_stride;
     d.prof_off = prof;
     d.qoff = q_offsets[q];
@@ -1282,8 +1288,10 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
     delete Q;
     return fail(SW_EINVAL, "sw_queries_prepare: profile chunk too large for shared memory");
   }
-  const int occ = cached_occupancy(0, R, packed ? kFormPacked : kFormInt32, threads, Q->smem);
-  const int occ32 = cached_occupancy(0, R, kFormInt32, threads, Q->smem);
+  Q->solo_form = packed ? (kFormPacked | (kWideSolo ? kFormWide : 0)) : kFormInt32;
+  Q->rescue_form = packed && kWideSolo ? (kFormInt32 | kFormWide) : kFormInt32;
+  const int occ = cached_occupancy(0, R, Q->solo_form, threads, Q->smem);
+  const int occ32 = cached_occupancy(0, R, Q->rescue_form, threads, Q->smem);
   const int occp = Q->n_ptasks ? cached_occupancy(0, R, kFormQPair, threads, Q->psmem) : 1;
   if (occ <= 0 || occ32 <= 0 || occp <= 0) {
     delete Q;
@@ -1638,7 +1646,7 @@ int sw_search_prepared(const sw_db *db, const sw_queries *Q, int32_t *scores_dev
     a.flag_pos = Q->d_flag_pos;
     a.flag_stride = db->n;
     a.flag_size = Q->inter_may_flag ? Q->nq * db->n : 0;
-    SW_CUDA(launch_inter(a, Q->R, packed ? kFormPacked : kFormInt32, Q->grid, threads, Q->smem, s), "inter-task kernel");
+    SW_CUDA(launch_inter(a, Q->R, Q->solo_form, Q->grid, threads, Q->smem, s), "inter-task kernel");
   }
   if (Q->timing && !band_timing && (Q->n_tasks || Q->n_ptasks)) {
     SW_CUDA(cudaEventRecord(Q->ev1, s), "event");
@@ -1657,7 +1665,7 @@ int sw_search_prepared(const sw_db *db, const sw_queries *Q, int32_t *scores_dev
       r.task_counter = w + 1;
       r.flag_count = nullptr;
       r.flag_pos = nullptr;
-      SW_CUDA(launch_inter(r, Q->R, kFormInt32, Q->rgrid, threads, Q->smem, s), "inter-task rescue kernel");
+      SW_CUDA(launch_inter(r, Q->R, Q->rescue_form, Q->rgrid, threads, Q->smem, s), "inter-task rescue kernel");
     }
   }
   if (Q->side) SW_CUDA(cudaStreamWaitEvent(s, Q->join, 0), "event");

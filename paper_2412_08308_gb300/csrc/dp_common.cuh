@@ -102,6 +102,20 @@ __host__ __device__ constexpr uint32_t sel_sext(int i) {
   return (uint32_t)i | ((uint32_t)(i | 8) << 4) | ((uint32_t)(i | 8) << 8) | ((uint32_t)(i | 8) << 12);
 }
 __host__ __device__ constexpr uint32_t sel_one(int i) { return 0x4440u | (uint32_t)i; }
+// the low 16-bit half of a, sign-extended to 32 bits
+__host__ __device__ constexpr uint32_t sel_sext16() { return 0x9910u; }
+
+// R 32-bit profile entries of one residue in the wide layout (R/4 16-byte
+// groups, `gstride` bytes apart: the lanes' groups interleaved)
+template <int N>
+__device__ __forceinline__ void load_groups(const uint8_t *p, int gstride, uint32_t (&w)[N]) {
+  static_assert(N % 4 == 0, "whole groups");
+#pragma unroll
+  for (int i = 0; i < N / 4; ++i) {
+    const uint4 v = *reinterpret_cast<const uint4 *>(p + i * gstride);
+    w[4 * i + 0] = v.x; w[4 * i + 1] = v.y; w[4 * i + 2] = v.z; w[4 * i + 3] = v.w;
+  }
+}
 
 template <int R>
 __device__ __forceinline__ void load_prof(const uint8_t *p, uint32_t (&w)[R / 4]) {
@@ -213,13 +227,15 @@ using Word = typename std::conditional<FORM != kFormInt32, uint32_t, int32_t>::t
 // and F of that row at this column (replaced by those of row R0 + N - 1); pb
 // the rows' profile bytes, four per word; E and Hl hold the previous column's
 // E and H per row and are updated in place; S keeps the running best.
-template <int R0, int N, int R>
-__device__ __forceinline__ void int_rows(int32_t hul, const uint32_t (&pb)[N / 4], int32_t (&E)[R], int32_t (&Hl)[R],
-                                         int32_t &hu, int32_t &fu, int32_t &S, const Consts &cs) {
-  static_assert(R0 + N <= R && N % 4 == 0, "rows in range, whole profile words");
+// sm_of(r): the substitution score of row R0 + r (one sign extension on the
+// ALU pipe from a profile byte, or from the low half of a 32-bit entry).
+template <int R0, int N, int R, class SmOf>
+__device__ __forceinline__ void int_rows_of(int32_t hul, SmOf sm_of, int32_t (&E)[R], int32_t (&Hl)[R], int32_t &hu,
+                                            int32_t &fu, int32_t &S, const Consts &cs) {
+  static_assert(R0 + N <= R, "rows in range");
 #pragma unroll
   for (int r = 0; r < N; ++r) {
-    const int32_t sm = (int32_t)prmt(pb[r >> 2], 0u, sel_sext(r & 3));
+    const int32_t sm = sm_of(r);
     const int32_t e1 = E[R0 + r] - cs.ge;
     const int32_t e2 = Hl[R0 + r] - cs.go;
     const int32_t e = max(e1, e2);
@@ -237,6 +253,14 @@ __device__ __forceinline__ void int_rows(int32_t hul, const uint32_t (&pb)[N / 4
     hu = h;
     fu = f;
   }
+}
+
+template <int R0, int N, int R>
+__device__ __forceinline__ void int_rows(int32_t hul, const uint32_t (&pb)[N / 4], int32_t (&E)[R], int32_t (&Hl)[R],
+                                         int32_t &hu, int32_t &fu, int32_t &S, const Consts &cs) {
+  static_assert(N % 4 == 0, "whole profile words");
+  int_rows_of<R0, N, R>(hul, [&](int r) { return (int32_t)prmt(pb[r >> 2], 0u, sel_sext(r & 3)); }, E, Hl, hu, fu, S,
+                        cs);
 }
 
 // int_rows with the one-operation F chain of word_rows_short, for the int32
@@ -303,7 +327,11 @@ __device__ __forceinline__ void lane_reset(LaneState<R, FORM> &st, const Consts 
 // Outputs the (H, F) pair for the row below: int32 passes (H, F) of the last
 // row; packed passes (H of the last row, F of the row below it).
 // SHORTF: rows by word_rows_short / int_rows_short, the one-operation chain.
-template <int R, int FORM, bool SHORTF = false>
+// WIDE (two-sequence and int32 forms): the profile holds 32-bit entries, the
+// score in the low 16-bit half (zero-extended), in the query-pair form's
+// group layout; the two sequences' entries are paired by one multiply-add
+// (FMA pipe) instead of a byte shuffle (ALU pipe).
+template <int R, int FORM, bool SHORTF = false, bool WIDE = false>
 __device__ __forceinline__ void column_step(LaneState<R, FORM> &st, const uint8_t *prow, int stride,
                                             uint32_t res, Word<FORM> inH, Word<FORM> inF, const Consts &cs,
                                             Word<FORM> &S, Word<FORM> &outH, Word<FORM> &outF, int gstride = 0) {
@@ -323,18 +351,36 @@ __device__ __forceinline__ void column_step(LaneState<R, FORM> &st, const uint8_
     outH = st.Hl[R - 1];
     outF = (W)f;
   } else if constexpr (FORM == kFormPacked) {
-    uint32_t pa[R / 4], pb[R / 4];
-    load_prof<R>(prow + (res & 0xffu) * stride, pa);
-    load_prof<R>(prow + (res >> 16) * stride, pb);
     uint32_t pw[R];
+    if constexpr (WIDE) {
+      uint32_t pa[R], pb[R];
+      load_groups<R>(prow + (res & 0xffu) * stride, gstride, pa);
+      load_groups<R>(prow + (res >> 16) * stride, gstride, pb);
 #pragma unroll
-    for (int r = 0; r < R; ++r) pw[r] = prmt(pa[r >> 2], pb[r >> 2], sel_pair(r & 3));  // (SM_a, SM_b), signed halves
+      for (int r = 0; r < R; ++r) pw[r] = pb[r] * 0x10000u + pa[r];  // (SM_a, SM_b)
+    } else {
+      uint32_t pa[R / 4], pb[R / 4];
+      load_prof<R>(prow + (res & 0xffu) * stride, pa);
+      load_prof<R>(prow + (res >> 16) * stride, pb);
+#pragma unroll
+      for (int r = 0; r < R; ++r) pw[r] = prmt(pa[r >> 2], pb[r >> 2], sel_pair(r & 3));  // (SM_a, SM_b), signed halves
+    }
     uint32_t f = (uint32_t)inF, s = (uint32_t)S;
     if constexpr (SHORTF) word_rows_short<0, R>((uint32_t)st.hdiag, pw, st.E, st.Hl, f, s, cs);
     else word_rows<0, R>((uint32_t)st.hdiag, pw, st.E, st.Hl, f, s, cs);
     S = (W)s;
     outH = st.Hl[R - 1];
     outF = (W)f;
+  } else if constexpr (WIDE) {
+    static_assert(!SHORTF, "the wide int32 rows follow Algorithm 1");
+    uint32_t pw[R];
+    load_groups<R>(prow + (res & 0xffu) * stride, gstride, pw);
+    int32_t hu = inH, fu = inF, s = S;
+    int_rows_of<0, R, R>(st.hdiag, [&](int r) { return (int32_t)prmt(pw[r], 0u, sel_sext16()); }, st.E, st.Hl, hu,
+                         fu, s, cs);
+    S = (W)s;
+    outH = (W)hu;
+    outF = (W)fu;
   } else {
     uint32_t pa[R / 4];
     load_prof<R>(prow + (res & 0xffu) * stride, pa);
@@ -355,7 +401,7 @@ __device__ __forceinline__ void column_step(LaneState<R, FORM> &st, const uint8_
 // the lane passes on the lower half's bottom row, of column c - 1, so lane
 // k + 1 works two columns behind lane k.  resA / resB: the residue code(s) of
 // column c / c - 1.  S and S2 keep the halves' running best.
-template <int R, int FORM>
+template <int R, int FORM, bool WIDE = false>
 __device__ __forceinline__ void column_step_split(LaneState<R, FORM> &st, uint32_t &hdiagB, uint32_t &midF,
                                                   const uint8_t *prow, int stride, uint32_t resA, uint32_t resB,
                                                   uint32_t inH, uint32_t inF, const Consts &cs, uint32_t &S,
@@ -371,6 +417,18 @@ __device__ __forceinline__ void column_step_split(LaneState<R, FORM> &st, uint32
       pa[4 * i + 0] = v.x; pa[4 * i + 1] = v.y; pa[4 * i + 2] = v.z; pa[4 * i + 3] = v.w;
       const uint4 w = *reinterpret_cast<const uint4 *>(prow + resB * stride + (H2 / 4 + i) * gstride);
       pb[4 * i + 0] = w.x; pb[4 * i + 1] = w.y; pb[4 * i + 2] = w.z; pb[4 * i + 3] = w.w;
+    }
+  } else if constexpr (WIDE) {
+    // two database sequences, 32-bit entries: each word pairs them by one multiply-add
+    uint32_t a0[H2], a1[H2], b0[H2], b1[H2];
+    load_groups<H2>(prow + (resA & 0xffu) * stride, gstride, a0);
+    load_groups<H2>(prow + (resA >> 16) * stride, gstride, a1);
+    load_groups<H2>(prow + (resB & 0xffu) * stride + (H2 / 4) * gstride, gstride, b0);
+    load_groups<H2>(prow + (resB >> 16) * stride + (H2 / 4) * gstride, gstride, b1);
+#pragma unroll
+    for (int r = 0; r < H2; ++r) {
+      pa[r] = a1[r] * 0x10000u + a0[r];
+      pb[r] = b1[r] * 0x10000u + b0[r];
     }
   } else {
     // two database sequences: each word pairs their profile bytes (PRMT)

@@ -37,7 +37,8 @@ struct QDesc {
   int64_t prof_off;  // byte offset of chunk 0 in the profile buffer
   int64_t qoff;      // offset of the query residues in the query residue buffer
   int32_t track_off; // track plans: index of the plan's first TrackChunk
-  int32_t pad_;
+  int32_t wide;      // solo plans: 1 = 32-bit entries (the score zero-extended in the low
+                     // half) in the query-pair group layout; 0 = bytes
 };
 
 // Query tracks (query-pair form).  The two 16-bit halves of a chain each run
@@ -66,6 +67,10 @@ __host__ __device__ inline int profile_slots(int L) { return L >= 32 ? L : (32 /
 constexpr int kFormInt32 = 0;   // one database sequence per chain, 32-bit cells
 constexpr int kFormPacked = 1;  // two database sequences per chain, 16-bit halves
 constexpr int kFormQPair = 2;   // two queries per chain (one sequence), 16-bit halves
+// host flag on kFormInt32 / kFormPacked for launch_inter and
+// inter_max_ctas_per_sm: the queries' profiles hold 32-bit entries (the score
+// zero-extended in the low half) in the query-pair form's group layout
+constexpr int kFormWide = 16;
 constexpr int32_t kStatusSaturated = 100;  // device status: a lane that could not saturate did
 constexpr int32_t kStatusBounds = 101;     // device status (checked build): an index left its buffer
 

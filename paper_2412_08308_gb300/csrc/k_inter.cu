@@ -59,7 +59,7 @@ __host__ __device__ constexpr int chain_lag(int L) { return kSplit<R, FORM> ? 2 
 // One pass of a chain over all columns of its unit for the rows of one chunk.
 // restart (16-bit forms): halves whose rows start a new query in this chunk;
 // they take the matrix top boundary instead of the strip of the chunk above.
-template <int R, int FORM>
+template <int R, int FORM, bool WIDE>
 __device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, const int stride, const int L,
                                            const int k, const int lane, const int slot, const int gstride,
                                            const bool live, const int nblk,
@@ -88,8 +88,9 @@ __device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, cons
   const bool tail = live && (k == L - 1) && next;
   uint8_t *rres = ring;                                  // [slot][seq][16 B]
   uint2 *rgb = reinterpret_cast<uint2 *>(ring + 64);     // [slot][16]
-  // this lane's profile slot: R bytes, or (query pairs) R/4 16-byte groups gstride apart
-  const uint8_t *prow = FORM == kFormQPair ? pch + slot * 16 : pch + slot * R;
+  // this lane's profile slot: R bytes, or (query pairs, wide entries) R/4
+  // 16-byte groups gstride apart
+  const uint8_t *prow = (FORM == kFormQPair || WIDE) ? pch + slot * 16 : pch + slot * R;
 
   auto prefetch = [&](int blk) {
     const int slot = blk & 1;
@@ -159,7 +160,7 @@ __device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, cons
         if constexpr (kChecked) inRes = checked_codes<FORM>(inRes, status);
         if constexpr (SPLIT) {
           uint32_t s = (uint32_t)S, oh, of;
-          column_step_split<R, FORM>(st, hdiagB, midF, prow, stride, inRes, prevRes, (uint32_t)inH, (uint32_t)inF,
+          column_step_split<R, FORM, WIDE>(st, hdiagB, midF, prow, stride, inRes, prevRes, (uint32_t)inH, (uint32_t)inF,
                                      cs, s, S2, oh, of, gstride);
           S = (W)s;
           outH = (W)oh;
@@ -167,7 +168,7 @@ __device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, cons
           outRes = prevRes;
           prevRes = inRes;
         } else {
-          column_step<R, FORM>(st, prow, stride, inRes, inH, inF, cs, S, outH, outF, gstride);
+          column_step<R, FORM, false, WIDE>(st, prow, stride, inRes, inH, inF, cs, S, outH, outF, gstride);
           outRes = inRes;
         }
         if (tail) {
@@ -186,7 +187,7 @@ __device__ __forceinline__ void chain_pass(const uint8_t *__restrict__ pch, cons
   if constexpr (SPLIT) S = score_max<FORM>(S, (W)S2);
 }
 
-template <int R, int FORM>
+template <int R, int FORM, bool WIDE>
 __global__ void __launch_bounds__(kThreads, 2) inter_kernel(const InterArgs a) {
   using W = Word<FORM>;
   constexpr bool PAIRS = FORM == kFormPacked;
@@ -280,7 +281,7 @@ __global__ void __launch_bounds__(kThreads, 2) inter_kernel(const InterArgs a) {
         if (threadIdx.x == 0) atomicExch(a.status, SW_ETIMEOUT);
         return;
       }
-      chain_pass<R, FORM>(pbuf + b * a.pbuf_bytes, qd.chunk_stride, L, k, lane, slot, gstride, live, nblk, npad,
+      chain_pass<R, FORM, WIDE>(pbuf + b * a.pbuf_bytes, qd.chunk_stride, L, k, lane, slot, gstride, live, nblk, npad,
                           npa, npb, resA, resB, ring, gb, c > 0, c + 1 < qd.nchunks, restart, cs, S,
                           a.db.res, a.db.res_bytes, a.gbuf_stride, a.status);
       __syncthreads();
@@ -317,18 +318,18 @@ __global__ void __launch_bounds__(kThreads, 2) inter_kernel(const InterArgs a) {
   }
 }
 
-template <int R, int FORM>
+template <int R, int FORM, bool WIDE>
 cudaError_t launch_one(const InterArgs &a, int grid, int threads, size_t smem, cudaStream_t s) {
-  inter_kernel<R, FORM><<<grid, threads, smem, s>>>(a);
+  inter_kernel<R, FORM, WIDE><<<grid, threads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 // Raise the dynamic shared-memory limit of an instantiation (done at plan time,
 // never inside a launch sequence that may be captured into a graph) and return
 // its resident CTAs per SM for the given block size and shared memory.
-template <int R, int FORM>
+template <int R, int FORM, bool WIDE>
 int configure_one(int threads, size_t smem) {
-  auto kern = inter_kernel<R, FORM>;
+  auto kern = inter_kernel<R, FORM, WIDE>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -359,6 +360,7 @@ bool inter_supported_R(int R) {
 }
 
 int inter_chain_lag(int R, int form, int L) {
+  form &= ~kFormWide;  // (the lag does not depend on the profile's entry width)
 #define SWGB_CASE(RR)                                                    \
   if (R == RR) {                                                         \
     if (form == kFormInt32) return chain_lag<RR, kFormInt32>(L);        \
@@ -372,11 +374,13 @@ int inter_chain_lag(int R, int form, int L) {
 
 cudaError_t launch_inter(const InterArgs &a, int R, int form, int grid, int threads, size_t smem,
                          cudaStream_t s) {
-#define SWGB_CASE(RR)                                                                   \
-  if (R == RR) {                                                                        \
-    if (form == kFormInt32) return launch_one<RR, kFormInt32>(a, grid, threads, smem, s);   \
-    if (form == kFormPacked) return launch_one<RR, kFormPacked>(a, grid, threads, smem, s); \
-    if (form == kFormQPair) return launch_one<RR, kFormQPair>(a, grid, threads, smem, s);   \
+#define SWGB_CASE(RR)                                                                                 \
+  if (R == RR) {                                                                                      \
+    if (form == kFormInt32) return launch_one<RR, kFormInt32, false>(a, grid, threads, smem, s);      \
+    if (form == kFormPacked) return launch_one<RR, kFormPacked, false>(a, grid, threads, smem, s);    \
+    if (form == kFormQPair) return launch_one<RR, kFormQPair, false>(a, grid, threads, smem, s);      \
+    if (form == (kFormInt32 | kFormWide)) return launch_one<RR, kFormInt32, true>(a, grid, threads, smem, s);   \
+    if (form == (kFormPacked | kFormWide)) return launch_one<RR, kFormPacked, true>(a, grid, threads, smem, s); \
   }
   SWGB_INTER_R_LIST(SWGB_CASE)
 #undef SWGB_CASE
@@ -384,11 +388,13 @@ cudaError_t launch_inter(const InterArgs &a, int R, int form, int grid, int thre
 }
 
 int inter_max_ctas_per_sm(int R, int form, int threads, size_t smem) {
-#define SWGB_CASE(RR)                                                                \
-  if (R == RR) {                                                                     \
-    if (form == kFormInt32) return configure_one<RR, kFormInt32>(threads, smem);     \
-    if (form == kFormPacked) return configure_one<RR, kFormPacked>(threads, smem);   \
-    if (form == kFormQPair) return configure_one<RR, kFormQPair>(threads, smem);     \
+#define SWGB_CASE(RR)                                                                              \
+  if (R == RR) {                                                                                   \
+    if (form == kFormInt32) return configure_one<RR, kFormInt32, false>(threads, smem);            \
+    if (form == kFormPacked) return configure_one<RR, kFormPacked, false>(threads, smem);          \
+    if (form == kFormQPair) return configure_one<RR, kFormQPair, false>(threads, smem);            \
+    if (form == (kFormInt32 | kFormWide)) return configure_one<RR, kFormInt32, true>(threads, smem);   \
+    if (form == (kFormPacked | kFormWide)) return configure_one<RR, kFormPacked, true>(threads, smem); \
   }
   SWGB_INTER_R_LIST(SWGB_CASE)
 #undef SWGB_CASE

@@ -24,6 +24,25 @@ __global__ void build_profiles_kernel(const uint8_t *__restrict__ qres, const QD
   const int slots = profile_slots(d.L);
   const int64_t words = (int64_t)d.nchunks * d.chunk_bytes / 4;
   uint32_t *out = reinterpret_cast<uint32_t *>(prof + d.prof_off);
+  if (d.wide) {
+    // 32-bit entries, the score zero-extended in the low half, in the group
+    // layout of the query-track profile below (word j of group i of slot s at
+    // word (i * slots + s) * 4 + j of the residue row: row (s mod L) * R +
+    // 4 i + j of the chunk)
+    const int cw = d.chunk_bytes / 4, rw = d.chunk_stride / 4;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words; w += (int64_t)gridDim.x * blockDim.x) {
+      const int c = (int)(w / cw);
+      const int rem = (int)(w - (int64_t)c * cw);
+      const int rho = rem / rw;
+      const int wi = rem - rho * rw;
+      const int gi = wi / (4 * slots), slot = (wi >> 2) - gi * slots;
+      const int x = (slot % d.L) * d.R + 4 * gi + (wi & 3);  // row within the chunk
+      int32_t val = pad;
+      if (wi < slots * d.R && rho < kAlphabet && c * LR + x < d.m) val = sm[q[c * LR + x] * kAlphabet + rho];
+      out[w] = (uint32_t)val & 0xffffu;
+    }
+    return;
+  }
   for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words; w += (int64_t)gridDim.x * blockDim.x) {
     const int64_t x0 = 4 * w;
     const int c = (int)(x0 / d.chunk_bytes);
