@@ -990,8 +990,9 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   //    balanced) and so that every resident CTA sees several tiles;
   //  - pairs: neighbours in length order whose shorter one has at least 3/4
   //    of the longer one's rows share a plan (one query per track); the
-  //    others keep the two-sequence form (7 instead of 6 ALU instructions per
-  //    word, two database sequences per chain).
+  //    others keep the two-sequence form (two database sequences per chain;
+  //    pairing their scores costs a seventh instruction per word, priced as
+  //    7/6 of the query-pair form's time per cell).
   // Each plan has its own lanes per chain.  (Many queries of similar length
   // favour pairs: each pair's L fits its length; few queries of spread-out
   // lengths favour tracks: no idle half.)
@@ -1035,7 +1036,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
     if (Lout) *Lout = Lp;
     return cost_of(Lp);
   };
-  auto solo_cost = [&](int32_t q) {  // two-sequence form: half the columns, 7/6 the instructions
+  auto solo_cost = [&](int32_t q) {  // two-sequence form: half the columns, 7/6 the instructions per word
     double best = 1e300;
     for (int L = 4; L <= 32; ++L) {
       const int C = chunks_of(q, L);
