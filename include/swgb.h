@@ -90,7 +90,14 @@ int sw_db_prepare(const uint8_t *residues, const int64_t *offsets, int64_t n_seq
  */
 int sw_db_free(sw_db *db);
 
-/* Sizes of a prepared database: sequence count, residue count, device bytes. */
+/*
+ * Sizes of a prepared database: sequence count, residue count, device bytes.
+ * The device bytes include the row-track lane tables the database keeps for
+ * the transposed jobs of small batches (sw_search): each is built on the
+ * first search that plans it (one per lane height and 16-bit / int32
+ * routing of the sequences, at most 8, each at most 64 MiB; others are built
+ * for every search) and freed by sw_db_free.
+ */
 int sw_db_stats(const sw_db *db, int64_t *n_seqs, int64_t *residues, int64_t *device_bytes);
 
 /* Tuning knobs of a query batch; zero-initialise and set what you need.  Every

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <limits>
 #include <memory>
 #include <mutex>
 #include <tuple>
@@ -153,6 +154,120 @@ bool is_device_ptr(const void *p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// --- the database in row tracks (transposed jobs, k_band.cu) ----------------
+// Sequences (sorted order, longest first), padded to whole lanes of tR rows,
+// go to the 16-bit tracks (f = 0; two tracks share each word) when their
+// length is at most `cut`, else to int32 tracks (f = 1).  A sequence longer
+// than a band (32 tR rows) gets a track of its own, whose bands run as a
+// pipeline; the others are packed into one-band tracks without crossing a
+// band boundary (each into the first of the last 64 open tracks with room),
+// so those bands depend on no other band.  Empty sequences score 0 without a
+// lane.
+struct TrackSeg {
+  int32_t pos, row0, rows, bin;  // sequence, first row in its track, rows (whole lanes), track
+};
+struct TrackBins {
+  std::vector<TrackSeg> seg[2];
+  std::vector<int32_t> used[2];  // rows of each track
+};
+// a pipeline of bands: one int32 track, or two 16-bit tracks sharing words
+struct TrackPipe {
+  int32_t packed, nb, lane0;
+};
+
+void bin_tracks(const std::vector<int32_t> &len, int tR, int32_t cut, TrackBins &b) {
+  const int32_t kRows = 32 * tR;  // rows per band
+  for (int f = 0; f < 2; ++f) {
+    b.seg[f].clear();
+    b.used[f].clear();
+  }
+  for (size_t k = 0; k < len.size(); ++k) {
+    if (len[k] == 0) continue;
+    const int f = len[k] <= cut ? 0 : 1;
+    const int32_t rows = (int32_t)round_up(len[k], tR);
+    std::vector<int32_t> &U = b.used[f];
+    if (rows > kRows) {
+      b.seg[f].push_back({(int32_t)k, 0, rows, (int32_t)U.size()});
+      U.push_back(rows);
+      continue;
+    }
+    size_t i = U.size();
+    for (size_t j = U.size() > 64 ? U.size() - 64 : 0; j < U.size(); ++j)
+      if (U[j] <= kRows - rows) {
+        i = j;
+        break;
+      }
+    if (i == U.size()) U.push_back(0);
+    b.seg[f].push_back({(int32_t)k, U[i], rows, (int32_t)i});
+    U[i] += rows;
+  }
+}
+
+// Bands of one query over all pipelines: the tracks ordered by band count
+// (longest first), 16-bit ones paired.
+int64_t track_bands(const TrackBins &b, int tR) {
+  const int32_t kRows = 32 * tR;
+  int64_t total = 0;
+  for (int f = 0; f < 2; ++f) {
+    std::vector<int32_t> nb(b.used[f].size());
+    for (size_t t = 0; t < nb.size(); ++t) nb[t] = (b.used[f][t] + kRows - 1) / kRows;
+    std::sort(nb.begin(), nb.end(), std::greater<int32_t>());
+    for (size_t i = 0; i < nb.size(); i += (f == 0 ? 2 : 1)) total += nb[i];
+  }
+  return total;
+}
+
+// The pipelines (deeper first; 16-bit ones pair consecutive tracks in that
+// order) and their lane table: band b, lane l of a pipeline covers rows
+// (32 b + l) tR .. + tR - 1 of its track(s); each segment writes its own
+// lanes (whole lanes from a lane boundary), the others stay idle.
+void lay_tracks(const TrackBins &b, int tR, std::vector<TrackPipe> &pipes, std::vector<TrackLane> &lanes) {
+  const int32_t kRows = 32 * tR;
+  pipes.clear();
+  lanes.clear();
+  for (int f = 0; f < 2; ++f) {
+    const std::vector<int32_t> &U = b.used[f];
+    const int32_t B = (int32_t)U.size();
+    auto bands = [&](int32_t t) { return (int32_t)((U[t] + kRows - 1) / kRows); };
+    std::vector<int32_t> order(B), base(B), high(B);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return bands(x) > bands(y); });
+    const int32_t step = f == 0 ? 2 : 1;
+    for (int32_t i = 0; i < B; i += step) {
+      const int32_t ta = order[i], tb = (f == 0 && i + 1 < B) ? order[i + 1] : -1;
+      const int32_t nb = std::max(bands(ta), tb >= 0 ? bands(tb) : 1);
+      TrackPipe pp{f == 0 ? 1 : 0, nb, (int32_t)lanes.size()};
+      base[ta] = pp.lane0;
+      high[ta] = 0;
+      if (tb >= 0) {
+        base[tb] = pp.lane0;
+        high[tb] = 1;
+      }
+      lanes.resize(lanes.size() + 32 * (size_t)nb, TrackLane{-1, 0, -1, 0});
+      pipes.push_back(pp);
+    }
+    for (const TrackSeg &g : b.seg[f]) {
+      TrackLane *L = lanes.data() + base[g.bin] + g.row0 / tR;
+      for (int32_t k = 0; k < g.rows / tR; ++k) {
+        if (high[g.bin]) {
+          L[k].pb = g.pos;
+          L[k].rb = k * tR;
+        } else {
+          L[k].pa = g.pos;
+          L[k].ra = k * tR;
+        }
+      }
+    }
+  }
+  std::stable_sort(pipes.begin(), pipes.end(), [](const TrackPipe &x, const TrackPipe &y) { return x.nb > y.nb; });
+}
+
+// Row-track layouts a database keeps (built on first use, its lane table on
+// the device): at most this many, each with at most this many bytes of lanes;
+// other layouts are built for every plan.
+constexpr size_t kTrackLayouts = 8;
+constexpr int64_t kTrackLayoutBytes = (int64_t)64 << 20;
+
 }  // namespace
 
 struct sw_db {
@@ -194,6 +309,56 @@ struct sw_db {
       }
     }
     return *u;
+  }
+  // transposed jobs: the database's row tracks for one lane height and one
+  // 16-bit / int32 routing (cut), with the lane table on the device, shared
+  // by every query batch that plans them
+  struct TrackLayout {
+    int32_t tR = 0, cut = 0;
+    int64_t bands = 0;    // bands of one query over all pipelines
+    int64_t n_lanes = 0;
+    std::vector<TrackPipe> pipes;
+    TrackLane *d_lanes = nullptr;
+  };
+  mutable std::mutex track_mu;
+  mutable std::vector<std::unique_ptr<TrackLayout>> track_layouts;
+  // the layout for (tR, cut), built and uploaded on stream s on first use
+  // (synchronising s), or nullptr: not kept (too large, too many, called on
+  // another device, or a CUDA error) -- the caller then builds it itself
+  const TrackLayout *track_layout(int tR, int32_t cut, cudaStream_t s) const {
+    std::lock_guard<std::mutex> lock(track_mu);
+    for (const std::unique_ptr<TrackLayout> &t : track_layouts)
+      if (t->tR == tR && t->cut == cut) return t.get();
+    int dev = -1;
+    if (track_layouts.size() >= kTrackLayouts || cudaGetDevice(&dev) != cudaSuccess || dev != device) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    // at most one lane per tR residues and one more per sequence
+    if ((total / tR + n) * (int64_t)sizeof(TrackLane) > kTrackLayoutBytes) return nullptr;
+    TrackBins b;
+    bin_tracks(h_len, tR, cut, b);
+    std::unique_ptr<TrackLayout> t(new TrackLayout());
+    t->tR = tR;
+    t->cut = cut;
+    std::vector<TrackLane> lanes;
+    lay_tracks(b, tR, t->pipes, lanes);
+    for (const TrackPipe &p : t->pipes) t->bands += p.nb;
+    t->n_lanes = (int64_t)lanes.size();
+    if (!lanes.empty()) {
+      void *d = nullptr;
+      cudaError_t e = cudaMalloc(&d, sizeof(TrackLane) * lanes.size());
+      if (e == cudaSuccess) e = cudaMemcpyAsync(d, lanes.data(), sizeof(TrackLane) * lanes.size(), cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) {
+        if (d) cudaFree(d);
+        cudaGetLastError();
+        return nullptr;
+      }
+      t->d_lanes = (TrackLane *)d;
+    }
+    track_layouts.push_back(std::move(t));
+    return track_layouts.back().get();
   }
 };
 
@@ -248,6 +413,7 @@ struct sw_queries {
   TrackJob *d_tjobs = nullptr;
   int32_t *d_tjob_of = nullptr;
   TrackLane *d_tlanes = nullptr;
+  bool tlanes_shared = false;  // d_tlanes is the database's kept lane table, not in the block
   uint8_t *d_qt = nullptr;
   int64_t *d_qt_off = nullptr;
   int32_t *d_qt_npad = nullptr;
@@ -418,6 +584,8 @@ int sw_db_free(sw_db *db) {
   g_err.clear();
   if (!db) return SW_OK;
   if (db->block) cudaFree(db->block);
+  for (const std::unique_ptr<sw_db::TrackLayout> &t : db->track_layouts)
+    if (t->d_lanes) cudaFree(t->d_lanes);
   delete db;
   return SW_OK;
 }
@@ -427,7 +595,13 @@ int sw_db_stats(const sw_db *db, int64_t *n_seqs, int64_t *residues, int64_t *de
   if (!db) return fail(SW_EINVAL, "sw_db_stats: null handle");
   if (n_seqs) *n_seqs = db->n;
   if (residues) *residues = db->total;
-  if (device_bytes) *device_bytes = (int64_t)db->bytes;
+  if (device_bytes) {
+    int64_t b = (int64_t)db->bytes;
+    std::lock_guard<std::mutex> lock(db->track_mu);
+    for (const std::unique_ptr<sw_db::TrackLayout> &t : db->track_layouts)
+      b += t->n_lanes * (int64_t)sizeof(TrackLane);
+    *device_bytes = b;
+  }
   return SW_OK;
 }
 
@@ -448,6 +622,8 @@ struct PlanScratch {
   std::vector<TrackJob> tjobs;
   std::vector<int32_t> tjob_of;
   std::vector<TrackLane> tlanes;
+  std::vector<TrackPipe> tpipes;
+  TrackBins bins;
   std::vector<TW> tw;
   std::vector<Task> tasks;
 };
@@ -460,6 +636,7 @@ PlanScratch &plan_scratch() {
   ps.tjobs.clear();
   ps.tjob_of.clear();
   ps.tlanes.clear();
+  ps.tpipes.clear();
   ps.tw.clear();
   ps.tasks.clear();
   return ps;
@@ -662,7 +839,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
     // alone (one short query) 16-row lanes are faster (0.081 against 0.084 ms)
     const int tRows = any_band ? 8 : kTrackRows;
     int tocc = any_track ? cached_occupancy(2, tRows, kTrackSplit ? 1 : 0, 0, 0) : 1;
-    int64_t ring = 0, band = 0, tring = 0, tband = 0;
+    int64_t ring = 0, band = 0, tring = 0, tband = 0, n_tlanes = 0;
     if (bocc > 0 && tocc > 0) {
       // band jobs: each band query against every unit
       struct BList {
@@ -766,9 +943,6 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
       }
 
       // transposed jobs: the database in row tracks, each short query as columns
-      struct Seg {
-        int32_t pos, row0, rows, bin;  // sequence, first row in its track, rows (whole lanes), track
-      };
       int32_t mtq = 0;
       int64_t qt = 0;
       int64_t n_track_q = 0;
@@ -781,108 +955,19 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
         qt += qt_npad[q];
       }
       Q->qt_bytes = std::max<int64_t>(qt, 16);
-      // tracks: a sequence longer than a band gets a track of its own (its
-      // bands run as a pipeline); the others, each padded to whole lanes,
-      // are packed into one-band tracks without crossing a band boundary
-      // (sorted longest first, each into the first of the last 64 open
-      // bands with room), so those bands depend on no other band.  Empty
-      // sequences score 0 without a job.
-      auto bin_tracks = [&](const int tR, std::vector<Seg> (&seg)[2], std::vector<int32_t> (&used)[2]) {
-        const int32_t kRows = 32 * tR;  // rows per band
-        for (int f = 0; f < 2; ++f) {
-          seg[f].clear();
-          used[f].clear();
-        }
-        for (int64_t k = 0; k < n; ++k) {
-          const int32_t len = db->h_len[k];
-          if (len == 0) continue;
-          const int f = (packed && (int64_t)sc.maxp * std::min<int32_t>(len, mtq) <= sc.thresh) ? 0 : 1;
-          const int32_t rows = (int32_t)round_up(len, tR);
-          std::vector<int32_t> &U = used[f];
-          if (rows > kRows) {
-            seg[f].push_back({(int32_t)k, 0, rows, (int32_t)U.size()});
-            U.push_back(rows);
-            continue;
-          }
-          size_t i = U.size();
-          for (size_t j = U.size() > 64 ? U.size() - 64 : 0; j < U.size(); ++j)
-            if (U[j] <= kRows - rows) {
-              i = j;
-              break;
-            }
-          if (i == U.size()) U.push_back(0);
-          seg[f].push_back({(int32_t)k, U[i], rows, (int32_t)i});
-          U[i] += rows;
-        }
-      };
-      // bands of all transposed jobs: the tracks ordered by band count
-      // (longest first), packed ones paired, each pipeline once per query
-      auto count_bands = [&](const int tR, const std::vector<int32_t> (&used)[2]) {
-        const int32_t kRows = 32 * tR;
-        int64_t total = 0;
-        for (int f = 0; f < 2; ++f) {
-          std::vector<int32_t> nb(used[f].size());
-          for (size_t t = 0; t < nb.size(); ++t) nb[t] = (used[f][t] + kRows - 1) / kRows;
-          std::sort(nb.begin(), nb.end(), std::greater<int32_t>());
-          for (size_t i = 0; i < nb.size(); i += (f == 0 ? 2 : 1)) total += nb[i];
-        }
-        return total * n_track_q;
-      };
-      auto build_tracks = [&](const int tR, const std::vector<Seg> (&seg)[2], const std::vector<int32_t> (&used)[2]) {
-        const int32_t kRows = 32 * tR;
+      // a sequence takes the 16-bit tracks (packed mode) unless its pair with
+      // the longest of these queries could pass the 16-bit range: a length
+      // cut that depends on the queries only through that longest one
+      const int32_t cut = !packed ? -1
+                          : (int64_t)sc.maxp * mtq <= sc.thresh ? std::numeric_limits<int32_t>::max()
+                                                                : sc.thresh / sc.maxp;
+      // the jobs: each pipeline once per query (deeper pipelines first)
+      auto make_jobs = [&](const std::vector<TrackPipe> &pipes) {
         tjobs.clear();
         tjob_of.clear();
-        tlanes.clear();
         tring = 0;
         tband = 0;
-        // pipelines: the tracks ordered by band count (longest first); packed
-        // ones pair consecutive tracks.  The lane table of a pipeline: band b,
-        // lane l covers rows (32 b + l) R .. + R - 1 of its track(s); each
-        // segment writes its own lanes (whole lanes from a lane boundary), the
-        // others stay idle
-        struct Pipe {
-          int32_t packed, nb, lane0;
-        };
-        std::vector<Pipe> pipes;
-        for (int f = 0; f < 2; ++f) {
-          const std::vector<int32_t> &U = used[f];
-          const int32_t B = (int32_t)U.size();
-          auto bands = [&](int32_t t) { return (int32_t)((U[t] + kRows - 1) / kRows); };
-          std::vector<int32_t> order(B), base(B), high(B);
-          std::iota(order.begin(), order.end(), 0);
-          std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return bands(x) > bands(y); });
-          const int32_t step = f == 0 ? 2 : 1;
-          for (int32_t i = 0; i < B; i += step) {
-            const int32_t ta = order[i], tb = (f == 0 && i + 1 < B) ? order[i + 1] : -1;
-            const int32_t nb = std::max(bands(ta), tb >= 0 ? bands(tb) : 1);
-            Pipe pp{f == 0 ? 1 : 0, nb, (int32_t)tlanes.size()};
-            base[ta] = pp.lane0;
-            high[ta] = 0;
-            if (tb >= 0) {
-              base[tb] = pp.lane0;
-              high[tb] = 1;
-            }
-            tlanes.resize(tlanes.size() + 32 * (size_t)nb, TrackLane{-1, 0, -1, 0});
-            pipes.push_back(pp);
-          }
-          for (const Seg &g : seg[f]) {
-            TrackLane *L = tlanes.data() + base[g.bin] + g.row0 / tR;
-            if (high[g.bin]) {
-              for (int32_t k = 0; k < g.rows / tR; ++k) {
-                L[k].pb = g.pos;
-                L[k].rb = k * tR;
-              }
-            } else {
-              for (int32_t k = 0; k < g.rows / tR; ++k) {
-                L[k].pa = g.pos;
-                L[k].ra = k * tR;
-              }
-            }
-          }
-        }
-        // deeper pipelines first
-        std::stable_sort(pipes.begin(), pipes.end(), [](const Pipe &x, const Pipe &y) { return x.nb > y.nb; });
-        for (const Pipe &pp : pipes)
+        for (const TrackPipe &pp : pipes)
           for (int64_t q = 0; q < n_queries; ++q) {
             if (!track_q[q]) continue;
             TrackJob j{};
@@ -905,34 +990,47 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
         // longer share the issue slots.  One 144-residue query x 2,000
         // proteins, packed: 0.081-0.085 -> 0.066 ms (32-row lanes the same);
         // int32 (twice the bands) and larger databases stay at 16 rows
-        // (8,000 proteins: 0.189 ms at 16 rows, 0.228 at 24)
-        std::vector<Seg> seg[2];
-        std::vector<int32_t> used[2];
+        // (8,000 proteins: 0.189 ms at 16 rows, 0.228 at 24).  The layouts
+        // come from the database's kept ones where it keeps them, so that
+        // repeated searches skip the binning and the lane upload.
+        TrackBins &bins = scratch.bins;
+        TrackBins bins24;
         int tR = tRows;
-        bin_tracks(tR, seg, used);
+        const sw_db::TrackLayout *lay = db->track_layout(tR, cut, s);
+        if (!lay) bin_tracks(db->h_len, tR, cut, bins);
         const int64_t subparts = 4 * (int64_t)sms;
-        const int64_t bands16 = (!any_band && tRows == 16) ? count_bands(16, used) : 0;
+        const int64_t bands16 =
+            (!any_band && tRows == 16) ? (lay ? lay->bands : track_bands(bins, 16)) * n_track_q : 0;
         if (bands16 > subparts && bands16 <= subparts * tocc) {
           const int occ24 = cached_occupancy(2, 24, 0, 0, 0);
-          std::vector<Seg> seg24[2];
-          std::vector<int32_t> used24[2];
-          if (occ24 > 0) bin_tracks(24, seg24, used24);
-          const int64_t bands24 = occ24 > 0 ? count_bands(24, used24) : 0;
+          const sw_db::TrackLayout *lay24 = nullptr;
+          int64_t bands24 = 0;
+          if (occ24 > 0) {
+            lay24 = db->track_layout(24, cut, s);
+            if (!lay24) bin_tracks(db->h_len, 24, cut, bins24);
+            bands24 = (lay24 ? lay24->bands : track_bands(bins24, 24)) * n_track_q;
+          }
           if (occ24 > 0 && bands24 <= subparts && bands24 <= (int64_t)sms * occ24 * (track_threads() / 32)) {
             tR = 24;
             tocc = occ24;
-            for (int f = 0; f < 2; ++f) {
-              seg[f].swap(seg24[f]);
-              used[f].swap(used24[f]);
-            }
+            lay = lay24;
+            if (!lay) std::swap(bins, bins24);
           }
         }
-        build_tracks(tR, seg, used);
+        if (lay) {
+          make_jobs(lay->pipes);
+          Q->d_tlanes = lay->d_lanes;  // the database's (not the batch's block)
+          n_tlanes = lay->n_lanes;
+        } else {
+          lay_tracks(bins, tR, scratch.tpipes, tlanes);
+          make_jobs(scratch.tpipes);
+          n_tlanes = (int64_t)tlanes.size();
+        }
         Q->tR = tR;
       }
       const int64_t kBandRingBudget = (int64_t)4 << 30;
       band_mode = 8 * (ring + tring) <= kBandRingBudget && band + tband < ((int64_t)1 << 30) &&
-                  (int64_t)tlanes.size() < ((int64_t)1 << 31);
+                  n_tlanes < ((int64_t)1 << 31);
       if (band_mode) {
         Q->n_bjobs = (int64_t)bjobs.size();
         Q->n_bands = band;
@@ -944,7 +1042,8 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
         Q->bone = bocc == 1 && bmax > 1;
         Q->n_tjobs = (int64_t)tjobs.size();
         Q->n_tbands = tband;
-        Q->n_tlanes = (int64_t)tlanes.size();
+        Q->n_tlanes = n_tlanes;
+        Q->tlanes_shared = Q->d_tlanes != nullptr;
         Q->track_ring_bytes = 8 * tring;
         Q->tgrid = (int)std::max<int64_t>(1, std::min<int64_t>((tband + track_threads() / 32 - 1) / (track_threads() / 32),
                                                                (int64_t)sms * tocc));
@@ -960,6 +1059,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
       tjobs.clear();
       tjob_of.clear();
       tlanes.clear();
+      Q->d_tlanes = nullptr;
     }
   }
 
@@ -1342,7 +1442,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   const bool tmode = Q->n_tjobs > 0;
   const size_t b_tjobs = tmode ? round_up((int64_t)sizeof(TrackJob) * Q->n_tjobs, 256) : 0;
   const size_t b_tjobof = tmode ? round_up(4 * Q->n_tbands, 256) : 0;
-  const size_t b_tlanes = tmode ? round_up((int64_t)sizeof(TrackLane) * Q->n_tlanes, 256) : 0;
+  const size_t b_tlanes = tmode && !Q->tlanes_shared ? round_up((int64_t)sizeof(TrackLane) * Q->n_tlanes, 256) : 0;
   const size_t b_qt = tmode ? round_up(Q->qt_bytes, 256) : 0;
   const size_t b_qtoff = tmode ? round_up(8 * nqm, 256) : 0;
   const size_t b_qtnpad = tmode ? round_up(4 * nqm, 256) : 0;
@@ -1388,7 +1488,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   if (tmode) {
     Q->d_tjobs = (TrackJob *)take(b_tjobs);
     Q->d_tjob_of = (int32_t *)take(b_tjobof);
-    Q->d_tlanes = (TrackLane *)take(b_tlanes);
+    if (!Q->tlanes_shared) Q->d_tlanes = (TrackLane *)take(b_tlanes);
     Q->d_qt = take(b_qt);
     Q->d_qt_off = (int64_t *)take(b_qtoff);
     Q->d_qt_npad = (int32_t *)take(b_qtnpad);
@@ -1411,7 +1511,8 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
                  (int64_t)sizeof(Task) * (Q->n_tasks + Q->n_itasks + Q->n_itasks32 + Q->n_ptasks) +
                  4 * (int64_t)ipos32.size() + 16 + (int64_t)sizeof(BandJob) * Q->n_bjobs + 4 * Q->n_bands +
                  (int64_t)sizeof(int2) * Q->n_btargets + (int64_t)sizeof(TrackJob) * Q->n_tjobs + 4 * Q->n_tbands +
-                 (int64_t)sizeof(TrackLane) * Q->n_tlanes + (tmode ? Q->qt_bytes + 12 * n_queries : 0);
+                 (Q->tlanes_shared ? 0 : (int64_t)sizeof(TrackLane) * Q->n_tlanes) +
+                 (tmode ? Q->qt_bytes + 12 * n_queries : 0);
   e = cudaSuccess;
   if (q_offsets[n_queries] > 0)
     e = cudaMemcpyAsync(Q->d_qres, queries, q_offsets[n_queries], cudaMemcpyHostToDevice, s);
@@ -1452,7 +1553,7 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
     e = cudaMemcpyAsync(Q->d_tjobs, tjobs.data(), sizeof(TrackJob) * Q->n_tjobs, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(Q->d_tjob_of, tjob_of.data(), 4 * Q->n_tbands, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && !Q->tlanes_shared)
       e = cudaMemcpyAsync(Q->d_tlanes, tlanes.data(), sizeof(TrackLane) * Q->n_tlanes, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(Q->d_qt, qtbuf.data(), qtbuf.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(Q->d_qt_off, qt_off.data(), 8 * n_queries, cudaMemcpyHostToDevice, s);

@@ -667,3 +667,50 @@ def test_searches_from_several_threads(api):
         t.join()
     db.close()
     assert not errors, errors
+
+
+def test_kept_track_layouts(api):
+    # small batches of transposed jobs against one database: the first
+    # search of each lane height and 16-bit / int32 routing builds a lane
+    # table the database keeps (its device bytes grow), a repeat reuses it,
+    # and beyond eight kept tables a plan builds its own.  The routing cut
+    # moves with the largest substitution score: a 700-residue query under
+    # matrices whose largest entry is 52..63 sends sequences longer than
+    # (32767 - max) / max (629..519 residues) to int32 tracks.  Every score
+    # against the oracle.
+    rng = np.random.Generator(np.random.PCG64(8808))
+    lens = [int(x) for x in rng.integers(20, 480, size=180)] + [int(x) for x in rng.integers(480, 700, size=100)]
+    lens += [0, 1, 513, 900, 1100, 1700]
+    db_s = from_list([rng.integers(0, 20, size=L).astype(np.uint8) for L in lens])
+    db = api.Database.from_sequences(db_s)
+    q144 = from_list([rng.integers(0, 20, size=144).astype(np.uint8)])
+    q700 = from_list([rng.integers(0, 20, size=700).astype(np.uint8), rng.integers(0, 20, size=90).astype(np.uint8)])
+    mixed = from_list([rng.integers(0, 20, size=1100).astype(np.uint8), rng.integers(0, 20, size=60).astype(np.uint8)])
+
+    def run(q, sm, mode, opts=None):
+        pq = api.PreparedQueries(db, q.residues, q.offsets, sm, 10, 2, mode, opts=opts)
+        got = pq.search().cpu().numpy()
+        pq.status()
+        pq.close()
+        _assert_equal(got, oracle.scores(q, db_s, sm, 10, 2))
+        return db.stats()[2]
+
+    try:
+        b0 = db.stats()[2]
+        b1 = run(q144, BLOSUM62, "packed")
+        assert b1 > b0
+        assert run(q144, BLOSUM62, "packed") == b1  # reused
+        b2 = run(q144, BLOSUM62, "int32")
+        assert b2 > b1
+        sizes = []
+        for top in range(52, 64):
+            sm = BLOSUM62.copy()
+            sm[3, 3] = top
+            sizes.append(run(q700, sm, "packed"))
+        kept = [b2] + sizes
+        grown = sum(1 for a, b in zip(kept, kept[1:]) if b > a)
+        assert grown == 6, sizes  # eight tables kept in all, then none
+        assert run(mixed, BLOSUM62, "packed", api.options(band_stream="always")) == sizes[-1]
+        assert run(mixed, BLOSUM62, "int32", api.options(band_stream="always")) == sizes[-1]
+    finally:
+        db.close()
