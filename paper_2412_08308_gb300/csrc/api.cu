@@ -624,6 +624,7 @@ struct PlanScratch {
   std::vector<TrackLane> tlanes;
   std::vector<TrackPipe> tpipes;
   TrackBins bins;
+  std::vector<uint8_t> stage;  // the plan's upload, laid out like its device block
   std::vector<TW> tw;
   std::vector<Task> tasks;
 };
@@ -1463,6 +1464,8 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
     p += b;
     return r;
   };
+  // the regions the host fills come first, back to back, so that one copy
+  // uploads them (with the zeroed status words and their constants)
   Q->d_qres = take(b_qres);
   Q->d_submat = (int8_t *)take(b_sub);
   Q->d_qd = (QDesc *)take(b_qd);
@@ -1471,20 +1474,13 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
   Q->d_itasks = (Task *)take(b_itasks);
   Q->d_itasks32 = (Task *)take(b_itasks32);
   Q->d_ipos32 = (int32_t *)take(b_ipos32);
-  Q->d_rtasks = (Task *)take(b_rtasks);
-  Q->d_prof = take(b_prof);
-  Q->d_gbuf = (uint2 *)take(b_gbuf);
-  Q->d_igbuf = (uint2 *)take(b_igbuf);
   Q->d_words = (int32_t *)take(b_words);
-  Q->d_flag_pos = Q->inter_may_flag ? (int32_t *)take(b_flag) : nullptr;
-  Q->d_iflag_pos = packed ? (int32_t *)take(b_iflag) : nullptr;
   Q->d_qdp = (QDesc *)take(b_qdp);
   Q->d_track = (TrackChunk *)take(b_track);
   Q->d_ptasks = (Task *)take(b_ptasks);
   Q->d_bjobs = (BandJob *)take(b_bjobs);
   Q->d_bjob_of = (int32_t *)take(b_bjobof);
   Q->d_btpos = (int2 *)take(b_btpos);
-  Q->d_brings = Q->n_bjobs ? (unsigned long long *)take(b_brings) : nullptr;
   if (tmode) {
     Q->d_tjobs = (TrackJob *)take(b_tjobs);
     Q->d_tjob_of = (int32_t *)take(b_tjobof);
@@ -1492,8 +1488,17 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
     Q->d_qt = take(b_qt);
     Q->d_qt_off = (int64_t *)take(b_qtoff);
     Q->d_qt_npad = (int32_t *)take(b_qtnpad);
-    Q->d_trings = (unsigned long long *)take(b_trings);
   }
+  const size_t up_bytes = (size_t)(p - (uint8_t *)Q->block);
+  // device-only regions
+  Q->d_rtasks = (Task *)take(b_rtasks);
+  Q->d_prof = take(b_prof);
+  Q->d_gbuf = (uint2 *)take(b_gbuf);
+  Q->d_igbuf = (uint2 *)take(b_igbuf);
+  Q->d_flag_pos = Q->inter_may_flag ? (int32_t *)take(b_flag) : nullptr;
+  Q->d_iflag_pos = packed ? (int32_t *)take(b_iflag) : nullptr;
+  Q->d_brings = Q->n_bjobs ? (unsigned long long *)take(b_brings) : nullptr;
+  if (tmode) Q->d_trings = (unsigned long long *)take(b_trings);
   Q->d_upos = const_cast<int32_t *>(db->d_ident) + s0;  // the short sequences, in sorted order
   Q->n_upos = n + 1 - s0;
 
@@ -1513,55 +1518,46 @@ int sw_queries_prepare(const sw_db *db, const uint8_t *queries, const int64_t *q
                  (int64_t)sizeof(int2) * Q->n_btargets + (int64_t)sizeof(TrackJob) * Q->n_tjobs + 4 * Q->n_tbands +
                  (Q->tlanes_shared ? 0 : (int64_t)sizeof(TrackLane) * Q->n_tlanes) +
                  (tmode ? Q->qt_bytes + 12 * n_queries : 0);
-  e = cudaSuccess;
-  if (q_offsets[n_queries] > 0)
-    e = cudaMemcpyAsync(Q->d_qres, queries, q_offsets[n_queries], cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(Q->d_submat, submat, 400, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess && n_queries)
-    e = cudaMemcpyAsync(Q->d_qd, Q->qd.data(), sizeof(QDesc) * n_queries, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess && n_queries && n_long)
-    e = cudaMemcpyAsync(Q->d_qdi, Q->qdi.data(), sizeof(QDesc) * n_queries, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess && Q->n_tasks)
-    e = cudaMemcpyAsync(Q->d_tasks, tasks.data(), sizeof(Task) * Q->n_tasks, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess && Q->n_itasks)
-    e = cudaMemcpyAsync(Q->d_itasks, itasks.data(), sizeof(Task) * Q->n_itasks, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess && Q->n_itasks32) {
-    e = cudaMemcpyAsync(Q->d_itasks32, itasks32.data(), sizeof(Task) * Q->n_itasks32, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(Q->d_ipos32, ipos32.data(), 4 * ipos32.size(), cudaMemcpyHostToDevice, s);
+  // stage the host tables at their offsets in the block (the rest zero:
+  // padding and the status words) and upload them with one copy
+  std::vector<uint8_t> &stage = scratch.stage;
+  stage.assign(up_bytes, 0);
+  auto put = [&](const void *dst, const void *src, size_t bytes) {
+    if (bytes) memcpy(stage.data() + ((const uint8_t *)dst - (const uint8_t *)Q->block), src, bytes);
+  };
+  put(Q->d_qres, queries, (size_t)q_offsets[n_queries]);
+  put(Q->d_submat, submat, 400);
+  if (n_queries) put(Q->d_qd, Q->qd.data(), sizeof(QDesc) * n_queries);
+  if (n_queries && n_long) put(Q->d_qdi, Q->qdi.data(), sizeof(QDesc) * n_queries);
+  put(Q->d_tasks, tasks.data(), sizeof(Task) * Q->n_tasks);
+  put(Q->d_itasks, itasks.data(), sizeof(Task) * Q->n_itasks);
+  if (Q->n_itasks32) {
+    put(Q->d_itasks32, itasks32.data(), sizeof(Task) * Q->n_itasks32);
+    put(Q->d_ipos32, ipos32.data(), 4 * ipos32.size());
   }
-  if (e == cudaSuccess && Q->npairs) {
-    e = cudaMemcpyAsync(Q->d_qdp, Q->qdp.data(), sizeof(QDesc) * Q->npairs, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(Q->d_track, Q->track.data(), sizeof(TrackChunk) * Q->track.size(), cudaMemcpyHostToDevice,
-                          s);
-    if (e == cudaSuccess && Q->n_ptasks)
-      e = cudaMemcpyAsync(Q->d_ptasks, ptasks.data(), sizeof(Task) * Q->n_ptasks, cudaMemcpyHostToDevice, s);
+  if (Q->npairs) {
+    put(Q->d_qdp, Q->qdp.data(), sizeof(QDesc) * Q->npairs);
+    put(Q->d_track, Q->track.data(), sizeof(TrackChunk) * Q->track.size());
+    put(Q->d_ptasks, ptasks.data(), sizeof(Task) * Q->n_ptasks);
   }
-  if (e == cudaSuccess && Q->n_bjobs) {
-    e = cudaMemcpyAsync(Q->d_bjobs, bjobs.data(), sizeof(BandJob) * Q->n_bjobs, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(Q->d_bjob_of, bjob_of.data(), 4 * Q->n_bands, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(Q->d_btpos, btpos.data(), sizeof(int2) * Q->n_btargets, cudaMemcpyHostToDevice, s);
+  if (Q->n_bjobs) {
+    put(Q->d_bjobs, bjobs.data(), sizeof(BandJob) * Q->n_bjobs);
+    put(Q->d_bjob_of, bjob_of.data(), 4 * Q->n_bands);
+    put(Q->d_btpos, btpos.data(), sizeof(int2) * Q->n_btargets);
   }
-  std::vector<uint8_t> qtbuf;
-  if (e == cudaSuccess && tmode) {
-    qtbuf.assign((size_t)Q->qt_bytes, (uint8_t)kPadCode);
+  if (tmode) {
+    put(Q->d_tjobs, tjobs.data(), sizeof(TrackJob) * Q->n_tjobs);
+    put(Q->d_tjob_of, tjob_of.data(), 4 * Q->n_tbands);
+    if (!Q->tlanes_shared) put(Q->d_tlanes, tlanes.data(), sizeof(TrackLane) * Q->n_tlanes);
+    uint8_t *qtp = stage.data() + (Q->d_qt - (uint8_t *)Q->block);
+    memset(qtp, kPadCode, (size_t)Q->qt_bytes);
     for (int64_t q = 0; q < n_queries; ++q)
-      if (track_q[q] && qlen(q) > 0) memcpy(&qtbuf[qt_off[q]], queries + q_offsets[q], (size_t)qlen(q));
-    e = cudaMemcpyAsync(Q->d_tjobs, tjobs.data(), sizeof(TrackJob) * Q->n_tjobs, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(Q->d_tjob_of, tjob_of.data(), 4 * Q->n_tbands, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && !Q->tlanes_shared)
-      e = cudaMemcpyAsync(Q->d_tlanes, tlanes.data(), sizeof(TrackLane) * Q->n_tlanes, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(Q->d_qt, qtbuf.data(), qtbuf.size(), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(Q->d_qt_off, qt_off.data(), 8 * n_queries, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(Q->d_qt_npad, qt_npad.data(), 4 * n_queries, cudaMemcpyHostToDevice, s);
+      if (track_q[q] && qlen(q) > 0) memcpy(qtp + qt_off[q], queries + q_offsets[q], (size_t)qlen(q));
+    put(Q->d_qt_off, qt_off.data(), 8 * n_queries);
+    put(Q->d_qt_npad, qt_npad.data(), 4 * n_queries);
   }
-  if (e == cudaSuccess) e = cudaMemsetAsync(Q->d_words, 0, b_words, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(Q->d_words + Q->zero_words(), consts, sizeof consts, cudaMemcpyHostToDevice, s);
+  put(Q->d_words + Q->zero_words(), consts, sizeof consts);
+  e = cudaMemcpyAsync(Q->block, stage.data(), up_bytes, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && ((n_long && !band_mode) || Q->n_bjobs)) {
     e = cudaStreamCreateWithFlags(&Q->side, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&Q->fork, cudaEventDisableTiming);
