@@ -489,6 +489,11 @@ int64_t db_sorted_pos(const sw_db *db, int64_t caller_index) { return db->h_pos[
 int32_t db_sorted_len(const sw_db *db, int64_t pos) { return db->h_len[pos]; }
 int32_t db_sorted_npad(const sw_db *db, int64_t pos) { return db->h_npad[pos]; }
 int64_t db_sorted_off(const sw_db *db, int64_t pos) { return db->h_off[pos]; }
+cudaError_t pool_alloc(void **ptr, size_t bytes, cudaStream_t s) {
+  cudaMemPool_t pool = nullptr;
+  cudaError_t e = batch_pool(&pool);
+  return e == cudaSuccess ? cudaMallocFromPoolAsync(ptr, bytes, pool, s) : e;
+}
 int set_last_error(int code, const char *msg) { return fail(code, "%s", msg); }
 void clear_last_error() { g_err.clear(); }
 }  // namespace swgb
@@ -1890,7 +1895,7 @@ int sw_search(const sw_db *db, const uint8_t *queries, const int64_t *q_offsets,
   void *tmp = nullptr;
   const bool dev = count > 0 && is_device_ptr(scores_out);
   if (count > 0 && !dev) {
-    cudaError_t e = cudaMallocAsync(&tmp, 4 * count, s);
+    cudaError_t e = swgb::pool_alloc(&tmp, 4 * count, s);
     if (e != cudaSuccess) {
       free_queries(Q);
       return cuda_fail(e, "sw_search: score buffer");

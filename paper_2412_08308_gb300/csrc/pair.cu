@@ -172,7 +172,7 @@ extern "C" int sw_align_pair(const uint8_t *query, int64_t m, const uint8_t *tar
                      (long long)free_b);
   PairScratch sc;
   sc.s = s;
-  e = cudaMallocAsync(&sc.block, bytes, s);
+  e = pool_alloc(&sc.block, bytes, s);
   if (e != cudaSuccess) {
     sc.block = nullptr;
     return pair_cuda(e, "device allocation");

@@ -105,7 +105,7 @@ extern "C" int sw_traceback(const sw_db *db, const uint8_t *queries, const int64
   cudaStream_t s = (cudaStream_t)stream;
   TraceScratch sc;
   sc.s = s;
-  cudaError_t e = cudaMallocAsync(&sc.block, (size_t)bytes, s);
+  cudaError_t e = pool_alloc(&sc.block, (size_t)bytes, s);
   if (e != cudaSuccess) {
     sc.block = nullptr;
     return tr_cuda(e, "device allocation");
