@@ -17,6 +17,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "../../include/swgb.h"
+#include "host_pool.h"
 #include "internal.h"
 
 using namespace swgb;

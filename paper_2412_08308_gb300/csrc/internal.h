@@ -310,10 +310,6 @@ int64_t db_sorted_pos(const struct ::sw_db *db, int64_t caller_index);  // calle
 int32_t db_sorted_len(const struct ::sw_db *db, int64_t pos);           // true length at a sorted position
 int32_t db_sorted_npad(const struct ::sw_db *db, int64_t pos);          // padded length at a sorted position
 int64_t db_sorted_off(const struct ::sw_db *db, int64_t pos);           // residue offset at a sorted position
-// Stream-ordered allocation from the library's memory pool of the current
-// device (freed blocks stay reserved up to 1 GiB, so that the next
-// allocation maps no fresh memory); free with cudaFreeAsync.
-cudaError_t pool_alloc(void **ptr, size_t bytes, cudaStream_t s);
 // Record the thread's last error message (see sw_last_error) and return `code`.
 int set_last_error(int code, const char *msg);
 void clear_last_error();

@@ -5,6 +5,7 @@
 #include <cstring>
 #include <vector>
 
+#include "host_pool.h"
 #include "internal.h"
 #include "../../include/swgb.h"
 
