@@ -241,9 +241,11 @@ int sw_queries_info(const sw_queries *q, int64_t *h2d_bytes, int64_t *device_byt
  *               owned by the caller
  *   stream      stream for the work
  *
- * The call allocates and frees its own scratch and returns when the scores
- * are in place.  Errors: as sw_queries_prepare / sw_search_prepared, plus
- * SW_ETIMEOUT.
+ * The call allocates and frees its own scratch (the batch's block and, for
+ * host scores, a device score buffer, both from the library's stream-ordered
+ * memory pool of the current device, which keeps up to 1 GiB of freed blocks
+ * for the next call) and returns when the scores are in place.  Errors: as
+ * sw_queries_prepare / sw_search_prepared, plus SW_ETIMEOUT.
  */
 int sw_search(const sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int64_t n_queries,
               const int8_t *submat, int32_t gap_open, int32_t gap_extend, int32_t mode,
