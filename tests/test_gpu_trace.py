@@ -89,18 +89,24 @@ def test_many_hits_and_repeats(api):
     _check(api, from_list(seqs), from_list(qs), hits, BLOSUM62, 10, 2)
 
 
-def test_long_queries_several_rounds(api):
+@pytest.mark.parametrize("with_short", [False, True])
+def test_long_queries_several_rounds(api, with_short):
     # queries of 18 and 9 chunks of 512 rows: 8 warps per hit take the chunks
-    # in rounds, the last warp's rows passing to the first through the strip
+    # in rounds, the last warp's rows passing to the first through the
+    # strip; with_short: hits of a 1,500-residue query too (3 chunks, one
+    # round, five warps of its CTA idle), listed between the others
     rng = np.random.Generator(np.random.PCG64(95))
     q0 = rng.integers(0, 20, size=9000).astype(np.uint8)
     q1 = rng.integers(0, 20, size=4100).astype(np.uint8)
+    q2 = rng.integers(0, 20, size=1500).astype(np.uint8)
     t0 = np.concatenate([rng.integers(0, 20, size=100).astype(np.uint8), q0[2000:3200], q0[6000:6300]])
     t0[300:900:7] = (t0[300:900:7] + 3) % 20
-    t1 = np.concatenate([q1[3500:4100], rng.integers(0, 20, size=50).astype(np.uint8), q1[:400]])
+    t1 = np.concatenate([q1[3500:4100], rng.integers(0, 20, size=50).astype(np.uint8), q1[:400], q2[700:1100]])
     t2 = rng.integers(0, 20, size=777).astype(np.uint8)
-    _check(api, from_list([t0, t1, t2]), from_list([q0, q1]), [(0, 0), (0, 1), (0, 2), (1, 1), (1, 0), (1, 2)],
-           BLOSUM62, 10, 2)
+    hits = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 0), (1, 2)]
+    if with_short:
+        hits = [(2, 1), (0, 0), (2, 0), (0, 1), (0, 2), (2, 2), (1, 1), (1, 0), (1, 2)]
+    _check(api, from_list([t0, t1, t2]), from_list([q0, q1, q2]), hits, BLOSUM62, 10, 2)
 
 
 def test_invalid_hits(api):
