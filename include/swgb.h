@@ -148,7 +148,11 @@ typedef struct sw_options {
  * Memory: the batch's device scratch is one block from a stream-ordered
  * memory pool that the library creates for each device on first use (not
  * the device's default pool); blocks freed by sw_queries_free stay reserved
- * in that pool, up to 1 GiB, for later batches.  The planner keeps its host
+ * in that pool, up to 1 GiB, for later batches.  A batch too small to fill
+ * the GPU may also make the database build one of the row-track lane tables
+ * it keeps (see sw_db_stats; a cudaMalloc and a synchronisation of `stream`,
+ * once per table), so do not prepare batches on a device while another
+ * thread captures a CUDA graph in global mode.  The planner keeps its host
  * tables in per-thread buffers between calls.  Calls from several threads
  * are safe.
  *
